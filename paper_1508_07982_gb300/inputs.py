@@ -1,0 +1,178 @@
+"""Seeded synthetic workloads for the refined-grid D3Q19 lattice Boltzmann method.
+
+This module describes inputs only: domains, refinement regions, obstacles,
+boundary conditions, relaxation parameters and initial (rho, u) fields.  It
+holds none of the method's arithmetic.  Both the CUDA library (through its
+binding) and the plain CPU oracle consume the same case dicts, each marshalling
+them into its own C struct.
+
+Case dict keys:
+  root      (nx, ny, nz) root blocks (the octree roots, Sec. 3.2)
+  B         cells per block edge on every level (Sec. 4: equal cell count per block)
+  lmax      deepest level the refinement may create
+  collision "srt" | "trt" (Sec. 2)
+  rho0      reference density of the incompressible equilibrium (Eq. fequ)
+  bc        six faces x-, x+, y-, y+, z-, z+: "periodic" | "noslip" | "velocity"
+  bc_u      wall velocity per face (used by "velocity" faces)
+  spheres   obstacles (cx, cy, cz, r) in level-0 cell units; a cell whose centre
+            lies inside is a no-slip obstacle
+  regions   refinement regions ("box", level, lo3, hi3) | ("ball", level, c3, r):
+            a block below `level` that overlaps the region is split (Sec. 3.3)
+  lambda_e0, magic, accel   coarse relaxation rate, TRT magic parameter, body
+            acceleration on level 0 (Sec. 2.3 scales them per level)
+All coordinates are in level-0 cell units; cell (i, j, k) of level L has its
+centre at ((i + .5) / 2^L, ...).
+"""
+import math
+
+import numpy as np
+
+SEED = 20150827
+
+
+# --------------------------------------------------------------------------- cases
+
+def cavity_case(lid=0.05, lambda_e0=1.6, B=8):
+    """Lid-driven cavity, 32^3 coarse cells, centre [8,24)^3 refined once.
+
+    With B = 8 the roots are 4^3 blocks of 8^3 cells and the 2^3 central roots are
+    split, giving 28,672 coarse + 32,768 fine cells.  Lid z = top moves with
+    (lid, 0, 0); all other walls are no-slip (Sec. 5.2 benchmark boundaries).
+    """
+    n = 32 // B
+    return dict(root=(n, n, n), B=B, lmax=1, collision="trt", rho0=1.0,
+                bc=["noslip"] * 5 + ["velocity"],
+                bc_u=[(0.0, 0.0, 0.0)] * 5 + [(lid, 0.0, 0.0)],
+                spheres=[], regions=[("box", 1, (8, 8, 8), (24, 24, 24))],
+                lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0))
+
+
+def periodic_case(n=64, B=16, collision="srt", omega=1.9, regions=(), lmax=0):
+    """Fully periodic cube of n^3 level-0 cells (uniform unless regions refine it)."""
+    r = n // B
+    return dict(root=(r, r, r), B=B, lmax=lmax, collision=collision, rho0=1.0,
+                bc=["periodic"] * 6, bc_u=[(0.0, 0.0, 0.0)] * 6, spheres=[],
+                regions=list(regions), lambda_e0=omega, magic=3.0 / 16.0,
+                accel=(0.0, 0.0, 0.0))
+
+
+SPHERE_CHANNEL_RADII = (40.0, 24.0, 13.0)
+
+
+def sphere_channel_case(H=64, B=32, radii=SPHERE_CHANNEL_RADII, u_in=0.04, Re=100.0):
+    """Channel 4H x H x H past a sphere of radius 0.1 H at (H, H/2, H/2).
+
+    Four levels: blocks within radii[L-1] (level-0 cells, scaled with H/64) of
+    the sphere centre are refined towards level L.  Inlet x- and outlet x+ are
+    velocity walls with the plug (u_in, 0, 0); y and z are periodic.  The
+    relaxation rate follows from Re on the sphere diameter.
+    """
+    s = H / 64.0
+    c = (float(H), H / 2.0, H / 2.0)
+    nu0 = u_in * (0.2 * H) / Re
+    le0 = 1.0 / (3.0 * nu0 + 0.5)
+    regions = [("ball", L + 1, c, r * s) for L, r in enumerate(radii)]
+    return dict(root=(4 * H // B, H // B, H // B), B=B, lmax=len(radii), collision="trt",
+                rho0=1.0, bc=["velocity", "velocity", "periodic", "periodic", "periodic", "periodic"],
+                bc_u=[(u_in, 0.0, 0.0)] * 2 + [(0.0, 0.0, 0.0)] * 4,
+                spheres=[(c[0], c[1], c[2], 0.1 * H)], regions=regions,
+                lambda_e0=le0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0), u_init=(u_in, 0.0, 0.0))
+
+
+def plane_poiseuille_case(B=4, ny_roots=4, nxz_roots=1, where="bottom", lambda_e0=0.5, accel=1e-5):
+    """Plane Poiseuille flow (Sec. 5.1): no-slip plates at y = 0 and y = H, periodic x and z,
+    driven by a constant acceleration in x.  `where` refines one plate, both, or the middle."""
+    H = ny_roots * B
+    regs = []
+    if where in ("bottom", "both"):
+        regs.append(("box", 1, (0, 0, 0), (1e9, 0.5, 1e9)))
+    if where in ("top", "both"):
+        regs.append(("box", 1, (0, H - 0.5, 0), (1e9, H, 1e9)))
+    if where == "middle":
+        regs.append(("box", 1, (0, H / 2 - 0.5, 0), (1e9, H / 2 + 0.5, 1e9)))
+    return dict(root=(nxz_roots, ny_roots, nxz_roots), B=B, lmax=1, collision="trt", rho0=1.0,
+                bc=["periodic", "periodic", "noslip", "noslip", "periodic", "periodic"],
+                bc_u=[(0.0, 0.0, 0.0)] * 6, spheres=[], regions=regs,
+                lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(accel, 0.0, 0.0))
+
+
+# --------------------------------------------------------------------------- fields
+
+def _splitmix64(x):
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays."""
+    x = (x + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = x
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    return z ^ (z >> np.uint64(31))
+
+
+def cell_normal(seed, X, Y, Z):
+    """Standard normal deviate per cell, a pure function of (seed, x, y, z): counter-based,
+    so any subset of cells can be generated in any order (Box-Muller on two SplitMix64 draws)."""
+    with np.errstate(over="ignore"):
+        key = (np.asarray(X, np.int64).astype(np.uint64)
+               | (np.asarray(Y, np.int64).astype(np.uint64) << np.uint64(21))
+               | (np.asarray(Z, np.int64).astype(np.uint64) << np.uint64(42)))
+        h1 = _splitmix64(key ^ np.uint64(seed))
+        h2 = _splitmix64(h1 ^ np.uint64(0xD1B54A32D192ED03))
+    u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+    u2 = ((h2 >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def taylor_green_modes(seed=SEED, nmodes=8, kmax=4):
+    """Divergence-free Taylor-Green modes: integer wave vectors in {1..kmax}^3 and
+    amplitudes drawn N(0,1) then projected orthogonal to k."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    for _ in range(nmodes):
+        k = rng.integers(1, kmax + 1, size=3).astype(np.float64)
+        a = rng.standard_normal(3)
+        a -= k * (a @ k) / (k @ k)
+        modes.append((k, a))
+    return modes
+
+
+def _tg_velocity(modes, N, Xc, Yc, Zc):
+    X = 2.0 * math.pi * Xc / N
+    Y = 2.0 * math.pi * Yc / N
+    Z = 2.0 * math.pi * Zc / N
+    u = [np.zeros(np.shape(X)) for _ in range(3)]
+    for k, a in modes:
+        sx, cx = np.sin(k[0] * X), np.cos(k[0] * X)
+        sy, cy = np.sin(k[1] * Y), np.cos(k[1] * Y)
+        sz, cz = np.sin(k[2] * Z), np.cos(k[2] * Z)
+        u[0] += a[0] * cx * sy * sz
+        u[1] += a[1] * sx * cy * sz
+        u[2] += a[2] * sx * sy * cz
+    return u
+
+
+def taylor_green_field(N, seed=SEED, nmodes=8, kmax=4, umax=0.02, rho_sigma=1e-4):
+    """Initial field of the periodic workload: a sum of Taylor-Green modes scaled so that
+    max |u| over the N^3 level-0 cell centres is umax, and rho = 1 + N(0, rho_sigma^2).
+    Returns field(level, X, Y, Z) -> (rho, (ux, uy, uz)) for integer level-L coordinates."""
+    modes = taylor_green_modes(seed, nmodes, kmax)
+    peak = 0.0
+    ax = np.arange(N) + 0.5
+    for z0 in range(0, N, 16):
+        Zc, Yc, Xc = np.meshgrid(ax[z0:z0 + 16], ax, ax, indexing="ij")
+        u = _tg_velocity(modes, N, Xc, Yc, Zc)
+        peak = max(peak, float(np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2).max()))
+    scale = umax / peak
+
+    def field(level, X, Y, Z):
+        s = 2.0 ** -level
+        u = _tg_velocity(modes, N, (X + 0.5) * s, (Y + 0.5) * s, (Z + 0.5) * s)
+        rho = 1.0 + rho_sigma * cell_normal(seed, X, Y, Z) if level == 0 else \
+            1.0 + rho_sigma * cell_normal(seed + level, X, Y, Z)
+        return rho, (u[0] * scale, u[1] * scale, u[2] * scale)
+
+    return field
+
+
+def uniform_field(rho=1.0, u=(0.0, 0.0, 0.0)):
+    def field(level, X, Y, Z):
+        return rho, u
+    return field

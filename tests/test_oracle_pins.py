@@ -1,0 +1,521 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something other than itself: closed-form
+lattice moments, operator eigenvalues, the physical viscosity of a decaying
+shear wave, an independent np.roll implementation of the textbook uniform-grid
+LBM, exact conservation laws, the analytic Poiseuille profile the paper says
+the refined scheme reproduces to machine accuracy (Sec. 5.1), and the paper's
+printed pipe-Poiseuille table (tests/golden/pipe_poiseuille_table.txt).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1508_07982_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- lattice
+
+def test_lattice_d3q19_structure_and_isotropy(oracle_mod):
+    """D3Q19 (Sec. 2, Fig. 1): 1 rest, 6 face, 12 edge velocities, none across corners;
+    weights give the isotropic moments up to 4th order that the equilibrium needs."""
+    e, w, opp = oracle_mod.lattice()
+    n2 = (e * e).sum(1)
+    assert sorted(n2.tolist()) == [0] + [1] * 6 + [2] * 12
+    assert len({tuple(v) for v in e}) == 19
+    assert np.all(e[opp] == -e)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs(w @ e).max() < 1e-16
+    d = np.eye(3)
+    M2 = np.einsum("a,ai,aj->ij", w, e, e)
+    assert np.abs(M2 - d / 3).max() < 1e-15
+    M3 = np.einsum("a,ai,aj,ak->ijk", w, e, e, e)
+    assert np.abs(M3).max() < 1e-16
+    M4 = np.einsum("a,ai,aj,ak,al->ijkl", w, e, e, e, e)
+    iso = (np.einsum("ij,kl->ijkl", d, d) + np.einsum("ik,jl->ijkl", d, d)
+           + np.einsum("il,jk->ijkl", d, d)) / 9.0
+    assert np.abs(M4 - iso).max() < 1e-15
+
+
+def test_equilibrium_moments_closed_form(oracle_mod):
+    """Eq. (fequ): sum f^eq = rho, sum e f^eq = rho0 u, sum e e f^eq = rho/3 I + rho0 u u."""
+    e, w, opp = oracle_mod.lattice()
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = 1.0 + 0.1 * rng.standard_normal()
+        rho0 = 1.0 + 0.05 * rng.random()
+        u = 0.1 * rng.standard_normal(3)
+        f = oracle_mod.feq(rho, u, rho0)
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.abs(e.T @ f - rho0 * u).max() < 1e-15
+        Pi = np.einsum("a,ai,aj->ij", f, e, e)
+        assert np.abs(Pi - (rho / 3 * np.eye(3) + rho0 * np.outer(u, u))).max() < 1e-15
+
+
+# --------------------------------------------------------------------------- collision
+
+@pytest.mark.parametrize("coll", ["srt", "trt"])
+def test_collision_conserves_mass_and_momentum(oracle_mod, coll):
+    """Sec. 2: the collision conserves rho and rho0 u; the force of Sec. 2.1 adds rho0 a."""
+    e, w, opp = oracle_mod.lattice()
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        f = oracle_mod.feq(1.0, 0.05 * rng.standard_normal(3)) + 1e-3 * rng.standard_normal(19)
+        g = oracle_mod.collide(f, coll, 1.3, 0.7)
+        assert abs(g.sum() - f.sum()) < 1e-15
+        assert np.abs(e.T @ g - e.T @ f).max() < 1e-15
+        acc = 1e-4 * rng.standard_normal(3)
+        g = oracle_mod.collide(f, coll, 1.3, 0.7, acc)
+        assert abs(g.sum() - f.sum()) < 1e-15
+        assert np.abs(e.T @ g - e.T @ f - acc).max() < 1e-15
+
+
+def test_trt_relaxes_even_and_odd_parts_with_their_rates(oracle_mod):
+    """TRT operator (Sec. 2): with moments fixed, the symmetric part of f - f^eq is scaled by
+    (1 - lambda_e) and the antisymmetric part by (1 - lambda_o)."""
+    e, w, opp = oracle_mod.lattice()
+    rng = np.random.default_rng(3)
+    u = np.array([0.03, -0.02, 0.01])
+    feq = oracle_mod.feq(1.0, u)
+    r = rng.standard_normal(19)
+    even = 0.5 * (r + r[opp])
+    even -= w * even.sum() / w.sum()          # zero mass; symmetric parts carry no momentum
+    r = rng.standard_normal(19)
+    odd = 0.5 * (r - r[opp])
+    odd -= 3 * w * (e @ (e.T @ odd))           # zero momentum (sum_a w e e = I/3)
+    odd = 0.5 * (odd - odd[opp])
+    assert abs(even.sum()) < 1e-14 and np.abs(e.T @ odd).max() < 1e-14
+    le, lo = 1.37, 0.61
+    f = feq + 1e-3 * (even + odd)
+    g = oracle_mod.collide(f, "trt", le, lo)
+    expect = feq + 1e-3 * ((1 - le) * even + (1 - lo) * odd)
+    assert np.abs(g - expect).max() < 1e-15
+
+
+def test_trt_coincides_with_srt_for_equal_rates(oracle_mod):
+    """Sec. 2: lambda_e = lambda_o = omega turns TRT into SRT."""
+    rng = np.random.default_rng(4)
+    f = oracle_mod.feq(1.02, [0.01, 0.02, -0.03]) + 1e-3 * rng.standard_normal(19)
+    a = oracle_mod.collide(f, "srt", 1.7, 1.7, [1e-5, 0, 2e-5])
+    b = oracle_mod.collide(f, "trt", 1.7, 1.7, [1e-5, 0, 2e-5])
+    assert np.abs(a - b).max() < 1e-16
+
+
+@pytest.mark.parametrize("coll", ["srt", "trt"])
+def test_equilibrium_is_a_fixed_point(oracle_mod, coll):
+    f = oracle_mod.feq(1.01, [0.04, -0.01, 0.02])
+    g = oracle_mod.collide(f, coll, 1.9, 0.4)
+    assert np.abs(g - f).max() < 1e-15
+
+
+# --------------------------------------------------------------------------- level scaling
+
+def test_rate_scaling_keeps_viscosity(oracle_mod):
+    """Eq. (omega_scaling_0): nu_L dx_L^2 / dt_L must equal nu_0 with dx_L = dx_0/2^L and
+    dt_L = dt_0/2^L, i.e. (1/w_L - 1/2) = 2^L (1/w_0 - 1/2); the fine rate of the two-level
+    cavity is 2 w_c / (4 - w_c)."""
+    for w0 in (0.3, 1.0, 1.6, 1.9404, 1.99):
+        for L in range(6):
+            wL = oracle_mod.scale_rate(w0, L)
+            assert abs((1 / wL - 0.5) - 2 ** L * (1 / w0 - 0.5)) < 1e-12 * 2 ** L
+        assert abs(oracle_mod.scale_rate(w0, 1) - 2 * w0 / (4 - w0)) < 1e-15
+        # the general form, Eq. (omega_scaling), from any level K
+        for K in range(4):
+            wK = oracle_mod.scale_rate(w0, K)
+            for L in range(6):
+                gen = 2 ** (K + 1) * wK / (2 ** (L + 1) + (2 ** K - 2 ** L) * wK)
+                assert abs(gen - oracle_mod.scale_rate(w0, L)) < 1e-13
+
+
+def test_odd_rate_keeps_magic_parameter(oracle_mod):
+    """Eq. (lambda_oL) keeps Lambda_eo of Eq. (lambda_eo) fixed on every level; with
+    Lambda = 3/16 and lambda_e = 1.6 the odd rate is exactly 1/2 (and 4/5 for 4/3)."""
+    for le in (0.5, 1.0, 1.6, 1.9):
+        for magic in (3 / 16, 1 / 4, 1 / 12):
+            lo = oracle_mod.lambda_odd(le, magic)
+            assert abs((1 / le - 0.5) * (1 / lo - 0.5) - magic) < 1e-14
+    assert abs(oracle_mod.lambda_odd(1.6, 3 / 16) - 0.5) < 1e-15
+    assert abs(oracle_mod.lambda_odd(4 / 3, 3 / 16) - 0.8) < 1e-15
+
+
+def test_level_parameters_of_the_cavity(oracle_mod):
+    o = oracle_mod.Oracle(inputs.cavity_case())
+    le, lo, acc = o.params()
+    assert np.allclose(le, [1.6, 4 / 3], rtol=0, atol=1e-15)
+    assert np.allclose(lo, [0.5, 0.8], rtol=0, atol=1e-15)
+
+
+def test_force_scaling(oracle_mod):
+    """Eq. (force_scaling): a_L = a_0 / 2^L."""
+    c = inputs.plane_poiseuille_case(where="bottom", accel=3e-5)
+    o = oracle_mod.Oracle(c)
+    le, lo, acc = o.params()
+    assert o.nlev == 2
+    assert acc[0, 0] == 3e-5 and acc[1, 0] == 1.5e-5
+
+
+# --------------------------------------------------------------------------- uniform grid = textbook LBM
+
+def _textbook_run(f, e, w, opp, steps, coll, le, lo, acc, walls_y=False):
+    """Independent uniform-grid D3Q19 reference: np.roll streaming, halfway bounce-back at
+    y walls (the rolled-in values at y = 0 / y = ny-1 are replaced by the cell's own opposite
+    post-collision value), collision written with moment arrays."""
+    f = f.copy()
+    for _ in range(steps):
+        rho = f.sum(0)
+        j = np.einsum("ai,a...->i...", e.astype(float), f)
+        eu = np.einsum("ai,i...->a...", e.astype(float), j)
+        uu = (j * j).sum(0)
+        feq = w[:, None, None, None] * (rho[None] + 3 * eu + 4.5 * eu * eu - 1.5 * uu[None])
+        if coll == "srt":
+            post = f - le * (f - feq)
+        else:
+            fp, fm = 0.5 * (f + f[opp]), 0.5 * (f - f[opp])
+            ep, em = 0.5 * (feq + feq[opp]), 0.5 * (feq - feq[opp])
+            post = f - le * (fp - ep) - lo * (fm - em)
+        post = post + 3 * w[:, None, None, None] * (e.astype(float) @ np.asarray(acc))[:, None, None, None]
+        new = np.empty_like(post)
+        for a in range(19):
+            new[a] = np.roll(post[a], shift=(e[a, 2], e[a, 1], e[a, 0]), axis=(0, 1, 2))
+            if walls_y:
+                if e[a, 1] == 1:
+                    new[a][:, 0, :] = post[opp[a]][:, 0, :]
+                elif e[a, 1] == -1:
+                    new[a][:, -1, :] = post[opp[a]][:, -1, :]
+        f = new
+    return f
+
+
+@pytest.mark.parametrize("coll,walls", [("srt", False), ("trt", False), ("trt", True)])
+def test_uniform_grid_equals_textbook_lbm(oracle_mod, coll, walls):
+    """Lmax = 0 reduces the method to plain D3Q19 LBM on a uniform grid.  The domain is
+    12 x 8 x 4 (distinct extents catch transposed axes); random non-equilibrium start."""
+    e, w, opp = oracle_mod.lattice()
+    B = 4
+    case = dict(root=(3, 2, 1), B=B, lmax=0, collision=coll, rho0=1.0,
+                bc=["periodic"] * 2 + (["noslip"] * 2 if walls else ["periodic"] * 2) + ["periodic"] * 2,
+                bc_u=[(0, 0, 0)] * 6, spheres=[], regions=[])
+    o = oracle_mod.Oracle(case)
+    le, lo = 1.45, 0.83
+    acc = (2e-5, -1e-5, 3e-5)
+    o.set_params_explicit([le], [lo], [acc])
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 12, 8, 4
+    f0 = np.stack([w[a] * (1 + 0.01 * rng.standard_normal((nz, ny, nx))) for a in range(19)])
+    f0 += np.einsum("a,ai,i...->a...", w, e.astype(float), 0.03 * rng.standard_normal((3, nz, ny, nx)))
+    s, n, N = o.window(0)
+    full = np.full((n[2], n[1], n[0], 19), np.nan)
+    X, Y, Z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    iz, iy, ix = o.lookup(0, X, Y, Z)
+    full[iz, iy, ix, :] = np.moveaxis(f0, 0, -1)[Z, Y, X, :]
+    o.set_f(0, full)
+    o.step(7)
+    got = o.get_f(0)[iz, iy, ix, :]
+    ref = _textbook_run(f0, e, w, opp, 7, coll, le, lo, acc, walls_y=walls)
+    ref = np.moveaxis(ref, 0, -1)[Z, Y, X, :]
+    assert np.abs(got - ref).max() < 1e-15
+
+
+# --------------------------------------------------------------------------- viscosity pin
+
+def _shear_wave_decay(oracle_mod, level_of_run, steps):
+    """Amplitude ratio of u_x = U sin(2 pi y / Ny) after `steps` coarse steps."""
+    n = 32
+    regions = [("box", 1, (-1, -1, -1), (99, 99, 99))] if level_of_run == 1 else []
+    case = inputs.periodic_case(n=n, B=8, collision="trt", omega=1.2, regions=regions, lmax=level_of_run)
+    o = oracle_mod.Oracle(case)
+    U = 1e-4
+
+    def field(L, X, Y, Z):
+        y = (Y + 0.5) * 2.0 ** -L
+        return 1.0, (U * np.sin(2 * np.pi * y / n), 0.0 * y, 0.0 * y)
+
+    o.init_fields(field)
+    o.step(steps)
+    L = o.nlev - 1
+    X, Y, Z = o.coords(L)
+    rho, u = o.macro(L)
+    y = (Y + 0.5) * 2.0 ** -L
+    amp = (u[0] * np.sin(2 * np.pi * y / n)).sum() / (np.sin(2 * np.pi * y / n) ** 2).sum()
+    return amp / U
+
+
+def test_shear_wave_decays_with_the_paper_viscosity(oracle_mod):
+    """Eq. (viscosity_srt/trt): nu = (1/lambda_e - 1/2)/3; a shear wave decays like
+    exp(-nu k^2 t) up to the O(k^2) lattice error (here ~1e-3 relative in the rate).  The same
+    physical decay holds when the whole domain runs one level finer with the scaled rate."""
+    n, steps = 32, 80
+    nu = (1 / 1.2 - 0.5) / 3
+    k = 2 * np.pi / n
+    expect = math.exp(-nu * k * k * steps)
+    r0 = _shear_wave_decay(oracle_mod, 0, steps)
+    assert abs(math.log(r0) / math.log(expect) - 1) < 5e-3
+    r1 = _shear_wave_decay(oracle_mod, 1, steps)
+    assert abs(math.log(r1) / math.log(expect) - 1) < 5e-3
+
+
+def test_full_refinement_equals_uniform_fine_grid(oracle_mod):
+    """Refining every root once leaves level 0 empty; n coarse steps must equal 2n steps of a
+    uniform grid at the fine resolution with lambda_1, a_1 (brute force equality)."""
+    e, w, opp = oracle_mod.lattice()
+    field = inputs.taylor_green_field(8, nmodes=3, kmax=2, umax=0.03)
+    base = dict(B=4, collision="trt", rho0=1.0, bc=["periodic"] * 6, bc_u=[(0, 0, 0)] * 6, spheres=[],
+                lambda_e0=1.5, magic=3 / 16, accel=(1e-5, 0, -2e-5))
+    ref = oracle_mod.Oracle(dict(base, root=(2, 2, 2), lmax=1, regions=[("box", 1, (-1, -1, -1), (99, 99, 99))]))
+    assert ref.nlev == 2 and ref.num_fluid(0) == 0
+    fine = oracle_mod.Oracle(dict(base, root=(4, 4, 4), lmax=0, regions=[]))
+    le, lo, acc = ref.params()
+    fine.set_params_explicit([le[1]], [lo[1]], [acc[1]])
+
+    def f_fine(L, X, Y, Z):   # the same field evaluated at fine cell centres
+        rho, u = field(1, X, Y, Z)
+        return rho, u
+
+    ref.init_fields(field)
+    fine.init_fields(f_fine)
+    ref.step(6)
+    fine.step(12)
+    a = ref.get_f(1)
+    b = fine.get_f(0)
+    X, Y, Z = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    ia = ref.lookup(1, X, Y, Z)
+    ib = fine.lookup(0, X, Y, Z)
+    assert np.abs(a[ia] - b[ib]).max() < 1e-15
+
+
+# --------------------------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("region", [
+    ("box", 1, (8, -1, -1), (24, 99, 99)),      # slab: planar interfaces only
+    ("box", 1, (8, 8, -1), (24, 24, 99)),       # column: interface edges
+    ("box", 1, (8, 8, 8), (24, 24, 24)),        # box: edges and corners
+    ("ball", 2, (16, 16, 16), 6.0),             # three levels
+])
+def test_mass_and_momentum_conserved_across_interfaces(oracle_mod, region):
+    """Sec. 1: the volume-based scheme conserves mass and momentum.  Periodic box with a
+    divergence-free random flow; totals weighted by cell volume 8^-L."""
+    case = inputs.periodic_case(n=32, B=8, collision="trt", omega=1.6, regions=[region], lmax=region[1])
+    o = oracle_mod.Oracle(case)
+    o.init_fields(inputs.taylor_green_field(32))
+    m0 = o.mass_momentum()
+    o.step(20)
+    m1 = o.mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-13
+    scale = 0.02 * m0[0]
+    assert np.abs(m1[1:] - m0[1:]).max() / scale < 1e-12
+
+
+def test_cavity_conserves_mass(oracle_mod):
+    o = oracle_mod.Oracle(inputs.cavity_case())
+    o.init_fields(inputs.uniform_field())
+    m0 = o.mass_momentum()
+    o.step(30)
+    m1 = o.mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-13
+
+
+def test_uniform_flow_stays_uniform_across_interfaces(oracle_mod):
+    case = inputs.periodic_case(n=32, B=8, collision="trt", omega=1.6,
+                                regions=[("box", 1, (8, 8, 8), (24, 24, 24))], lmax=1)
+    o = oracle_mod.Oracle(case)
+    u0 = (0.03, -0.01, 0.02)
+    o.init_fields(inputs.uniform_field(u=u0))
+    o.step(10)
+    ref = oracle_mod.feq(1.0, u0)
+    for L in range(2):
+        cls, flg = o.classes(L)
+        own = (cls == 1) & (flg == 0)
+        f = o.get_f(L)[own]
+        assert np.abs(f - ref).max() < 1e-15
+
+
+def test_cavity_is_mirror_symmetric_in_y(oracle_mod):
+    """The lid moves along x, so the cavity flow is symmetric under y -> -y."""
+    e, w, opp = oracle_mod.lattice()
+    mirror = [int(np.where((e == e[a] * [1, -1, 1]).all(1))[0][0]) for a in range(19)]
+    o = oracle_mod.Oracle(inputs.cavity_case())
+    o.init_fields(inputs.uniform_field())
+    o.step(25)
+    for L in range(2):
+        X, Y, Z = o.coords(L)
+        cls, flg = o.classes(L)
+        own = (cls == 1) & (flg == 0)
+        N = 32 << L
+        f = o.get_f(L)
+        im = o.lookup(L, X[own], N - 1 - Y[own], Z[own])
+        assert np.abs(f[own] - f[im][:, mirror]).max() < 1e-15
+
+
+def test_cavity_interface_counts(oracle_mod):
+    """Cfg. cavity: 28,672 coarse and 32,768 fine cells; 40^3 - 32^3 fine ghost cells in layers
+    1-4; 36^3 fine cells stream; coalescence fills 5 PDFs in each of the 6 x 16^2 coarse cells
+    across a face of the fine box and 1 PDF in each of the 12 x 16 coarse cells across an edge."""
+    o = oracle_mod.Oracle(inputs.cavity_case())
+    c0, c1 = o.counts(0), o.counts(1)
+    assert c0["fluid"] == 28672 and c1["fluid"] == 32768
+    assert c1["ghost"] == 40 ** 3 - 32 ** 3
+    assert c1["stream"] == 36 ** 3
+    assert c0["coalesce"] == 6 * 16 * 16 * 5 + 12 * 16 * 1
+    assert o.cell_updates_per_coarse_step() == 28672 + 2 * 32768
+
+
+def test_block_size_does_not_change_the_result(oracle_mod):
+    field = inputs.taylor_green_field(32)
+    res = []
+    for B in (4, 8):
+        case = inputs.periodic_case(n=32, B=B, collision="trt", omega=1.7,
+                                    regions=[("box", 1, (16, 0, 8), (32, 16, 24))], lmax=1)
+        o = oracle_mod.Oracle(case)
+        o.init_fields(field)
+        o.step(5)
+        fine = []
+        for L in range(2):
+            cls, flg = o.classes(L)
+            X, Y, Z = o.coords(L)
+            own = (cls == 1) & (flg == 0)
+            key = np.lexsort((X[own], Y[own], Z[own]))
+            fine.append(o.get_f(L)[own][key])
+        res.append(fine)
+    for L in range(2):
+        assert res[0][L].shape == res[1][L].shape
+        assert np.abs(res[0][L] - res[1][L]).max() == 0.0
+
+
+# --------------------------------------------------------------------------- forest
+
+def _touching_leaf_levels(o, nroot, B, per):
+    """All (level, level) pairs of leaves that touch (face, edge or corner), by brute force on
+    the finest cell grid."""
+    nl = o.nlev
+    fine = np.full(tuple(int(r) * (1 << (nl - 1)) for r in nroot[::-1]), -1, np.int16)
+    for L in range(nl):
+        s = 1 << (nl - 1 - L)
+        for b in o.leaves(L):
+            fine[b[2] * s:(b[2] + 1) * s, b[1] * s:(b[1] + 1) * s, b[0] * s:(b[0] + 1) * s] = L
+    worst = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                sh = np.roll(fine, (dz, dy, dx), axis=(0, 1, 2))
+                valid = np.ones(fine.shape, bool)
+                for ax, d in zip((0, 1, 2), (dz, dy, dx)):
+                    if not per[2 - ax] and d != 0:
+                        idx = [slice(None)] * 3
+                        idx[ax] = 0 if d == 1 else -1
+                        valid[tuple(idx)] = False
+                worst = max(worst, int(np.abs(sh - fine)[valid].max()))
+    return fine, worst
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_forest_is_2to1_balanced_and_tiles_the_domain(oracle_mod, seed):
+    """Sec. 3.3: refinement by callback plus 2:1 balance across faces, edges and corners."""
+    rng = np.random.default_rng(seed)
+    nroot = rng.integers(1, 4, size=3)
+    per = [bool(rng.integers(0, 2)) for _ in range(3)]
+    marks = {}
+
+    def refine(L, bx, by, bz, user):
+        key = (L, bx, by, bz)
+        if key not in marks:
+            marks[key] = rng.random() < (0.35 if L == 0 else 0.15)
+        return int(marks[key])
+
+    bc = []
+    for a in range(3):
+        bc += ["periodic", "periodic"] if per[a] else ["noslip", "noslip"]
+    case = dict(root=tuple(int(v) for v in nroot), B=4, lmax=3, collision="trt", rho0=1.0, bc=bc,
+                bc_u=[(0, 0, 0)] * 6, spheres=[], regions=[])
+    o = oracle_mod.Oracle(case, refine=refine)
+    fine, worst = _touching_leaf_levels(o, nroot, 4, per)
+    assert (fine >= 0).all()                      # every finest cell is covered by exactly one leaf
+    vol = sum(len(o.leaves(L)) * 8.0 ** -L for L in range(o.nlev))
+    assert abs(vol - np.prod(nroot)) < 1e-12
+    assert worst <= 1
+    leaves = {(L, *map(int, b)) for L in range(o.nlev) for b in o.leaves(L)}
+    for key, m in marks.items():                  # every block the callback marked is split
+        if m and key[0] < 3:
+            assert key not in leaves
+
+
+# --------------------------------------------------------------------------- Poiseuille
+
+@pytest.mark.parametrize("where", ["bottom", "top", "both", "middle"])
+def test_refined_plane_poiseuille_reaches_machine_accuracy(oracle_mod, where):
+    """Sec. 5.1: TRT with Lambda = 3/16 reproduces plane Poiseuille flow exactly on uniform grids,
+    and with refinement at one plate, both plates or in the middle the error still drops to
+    values close to machine accuracy."""
+    le0, a = 0.5, 1e-5
+    case = inputs.plane_poiseuille_case(B=4, ny_roots=4, where=where, lambda_e0=le0, accel=a)
+    o = oracle_mod.Oracle(case)
+    assert o.nlev == 2 and o.num_fluid(0) > 0 and o.num_fluid(1) > 0
+    o.init_fields(inputs.uniform_field())
+    o.step(1700)
+    H = 16
+    nu0 = (1 / le0 - 0.5) / 3
+    umax = a * H * H / (8 * nu0)
+    err = 0.0
+    for L in range(2):
+        X, Y, Z = o.coords(L)
+        rho, u = o.macro(L)
+        cls, flg = o.classes(L)
+        own = (cls == 1) & (flg == 0)
+        y = (Y + 0.5) * 2.0 ** -L
+        exact = a * y * (H - y) / (2 * nu0)
+        err = max(err, np.abs(u[0] - exact)[own].max() / umax)
+        err = max(err, np.abs(u[1])[own].max() / umax, np.abs(u[2])[own].max() / umax)
+    assert err < 1e-10
+
+
+def _golden_pipe():
+    rows = {}
+    with open(os.path.join(GOLDEN, "pipe_poiseuille_table.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            p = line.split()
+            rows[(p[0], int(p[1]))] = [float(v) for v in p[2:]]
+    return rows
+
+
+def test_pipe_poiseuille_matches_the_paper_table(oracle_mod):
+    """Pipe Poiseuille, global refinement 0 (D = 60 level-0 cells, staircase by cell centre,
+    TRT Lambda = 3/16): flow-rate error and L1/L2/Linf of the steady state against the printed
+    table.  With Lambda fixed the normalised steady Stokes solution does not depend on the
+    viscosity, so a large viscosity reaches it quickly; the start is the analytic profile."""
+    R, le0, a = 30.0, 0.6, 1e-6
+    nu = (1 / le0 - 0.5) / 3
+    umax = a * R * R / (4 * nu)
+    case = dict(root=(1, 6, 6), B=10, lmax=0, collision="trt", rho0=1.0,
+                bc=["periodic"] * 2 + ["noslip"] * 4, bc_u=[(0, 0, 0)] * 6, spheres=[], regions=[],
+                lambda_e0=le0, magic=3 / 16, accel=(a, 0, 0))
+
+    def flag(L, x, y, z, user):
+        return 1 if (y - 30) ** 2 + (z - 30) ** 2 >= R * R else 0
+
+    def field(L, X, Y, Z):
+        y, z = Y + 0.5 - 30, Z + 0.5 - 30
+        u = np.maximum(umax * (1 - (y * y + z * z) / R ** 2), 0)
+        return 1.0, (u, 0 * u, 0 * u)
+
+    o = oracle_mod.Oracle(case, flag=flag)
+    o.init_fields(field)
+    o.step(2500)
+    X, Y, Z = o.coords(0)
+    rho, u = o.macro(0)
+    cls, flg = o.classes(0)
+    own = (cls == 1) & (flg == 0)
+    y, z = Y[own] + 0.5 - 30, Z[own] + 0.5 - 30
+    ue = 1 - (y * y + z * z) / R ** 2
+    du = np.sqrt((u[0][own] / umax - ue) ** 2 + (u[1][own] / umax) ** 2 + (u[2][own] / umax) ** 2)
+    w = (1 / 60) ** 3 * 6                  # cell volume; the 10-cell pipe section is 1/6 of [0,1]
+    Q = (u[0][own][X[own] == 5] / umax).sum() / 60 ** 2
+    Qe = math.pi / 8
+    got = [abs(Q - Qe) / Qe, (w * du).sum(), math.sqrt((w * du * du).sum()), du.max()]
+    want = _golden_pipe()[("global", 0)]
+    for g, p in zip(got, want):
+        assert abs(g - p) / p < 0.02, (got, want)
