@@ -1,0 +1,193 @@
+/*
+ * lbm_gb300.h -- C-ABI of the GB300-native refined-grid D3Q19 lattice Boltzmann library.
+ *
+ * The method is the volume-based grid refinement of Schornbaum & Ruede,
+ * "Massively parallel algorithms for the lattice Boltzmann method on non-uniform
+ * grids" (arXiv:1508.07982): D3Q19 SRT/TRT collision (Sec. 2), a 2:1-balanced
+ * forest of octrees of equal-sized blocks (Sec. 3.2-3.3), and the recursive level
+ * schedule of Alg. 1 / Alg. 2 (Sec. 4.1) with homogeneous explosion (Eq. ctof) and
+ * averaging coalescence (Eq. ftoc).  Every step of a time step runs in the library's
+ * own sm_103a CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions used by every call:
+ *  - Coordinates are in level-0 cell units.  Cell (i, j, k) of level L has its centre
+ *    at ((i + 0.5) / 2^L, (j + 0.5) / 2^L, (k + 0.5) / 2^L).
+ *  - PDF directions follow this fixed D3Q19 order (an interface convention, like a file
+ *    format):  0 (0,0,0); 1 (+1,0,0) 2 (-1,0,0) 3 (0,+1,0) 4 (0,-1,0) 5 (0,0,+1)
+ *    6 (0,0,-1); 7 (+1,+1,0) 8 (-1,-1,0) 9 (+1,-1,0) 10 (-1,+1,0) 11 (+1,0,+1)
+ *    12 (-1,0,-1) 13 (+1,0,-1) 14 (-1,0,+1) 15 (0,+1,+1) 16 (0,-1,-1) 17 (0,+1,-1)
+ *    18 (0,-1,+1).  Weights 1/3, 1/18 (faces), 1/36 (edges).
+ *  - Per-level cell arrays are "block-major": the level's leaf blocks in the order of
+ *    lbm_get_block_table, each block's B^3 cells in x-fastest, then y, then z order.
+ *  - Every call returns an lbm_status; no exception crosses the ABI.  On failure,
+ *    lbm_last_error() returns a thread-local description.
+ *  - Device memory is owned by the forest handle and released by lbm_destroy.
+ *    Caller buffers are owned by the caller.  `on_device` = 1 means a pointer is a CUDA
+ *    device pointer on the forest's device; 0 means host memory (pinned or pageable).
+ *  - `stream` is a cudaStream_t (0 = the legacy default stream).  Calls that launch work
+ *    are asynchronous on that stream unless stated otherwise; calls that return host
+ *    data synchronise the stream.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,       /* invalid argument or description */
+    LBM_EUNBALANCED = 2,  /* a forest check found a 2:1 balance violation (internal error) */
+    LBM_ENOMEM = 3,       /* device or host allocation failed */
+    LBM_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    LBM_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    LBM_ENONFINITE = 6    /* a reduction met a NaN or Inf */
+} lbm_status;
+
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_NOSLIP = 1, LBM_BC_VELOCITY = 2 } lbm_bc;
+typedef enum { LBM_SRT = 0, LBM_TRT = 1 } lbm_collision;
+
+/* PDF storage.  FP64 stores f_a; FP32S and FP16S store the shifted value f_a - w_a rho0 and
+ * collide in FP32; coalescence means and the mass/momentum totals accumulate in FP64. */
+typedef enum { LBM_FP64 = 0, LBM_FP32S = 1, LBM_FP16S = 2 } lbm_precision;
+
+#define LBM_MAX_LEVELS 8
+#define LBM_MAX_SPHERES 64
+#define LBM_MAX_REGIONS 64
+
+/* Domain and refinement description (Sec. 3.3: a uniform root grid whose blocks are split
+ * into 8 while marked by the application; the library adds the splits 2:1 balance needs).
+ *   root_blocks   number of root blocks per axis (>= 1)
+ *   block_cells   B, cells per block edge on every level: 8, 16 or 32
+ *   max_level     deepest level a split may create (0 .. LBM_MAX_LEVELS-1)
+ *   bc[6]         faces x-, x+, y-, y+, z-, z+; periodic faces come in pairs
+ *   bc_velocity   wall velocity of LBM_BC_VELOCITY faces (Sec. 5.2: velocity bounce-back)
+ *   rho0          reference density of the incompressible equilibrium (Eq. fequ)
+ *   spheres       no-slip obstacles (cx, cy, cz, r): a cell whose centre lies inside
+ *   regions       refinement regions: {kind, target level, p0..p5} with kind 0 = box
+ *                 (lo xyz, hi xyz) and kind 1 = ball (centre xyz, radius); a block of level
+ *                 L < target that overlaps the region (with positive volume, or closer than
+ *                 the radius) is split. */
+typedef struct {
+    int32_t root_blocks[3];
+    int32_t block_cells;
+    int32_t max_level;
+    int32_t precision;    /* lbm_precision */
+    int32_t collision;    /* lbm_collision */
+    int32_t bc[6];        /* lbm_bc */
+    double bc_velocity[6][3];
+    double rho0;
+    int32_t n_spheres;
+    double spheres[LBM_MAX_SPHERES][4];
+    int32_t n_regions;
+    double regions[LBM_MAX_REGIONS][8];
+} lbm_forest_desc;
+
+/* Application callbacks (Sec. 3.3).  refine: return nonzero to split block (bx, by, bz) of
+ * `level` (block coordinates of that level).  flag: return nonzero if the cell centred at
+ * (x, y, z) of `level` is a no-slip obstacle.  Both may be NULL and are only called during
+ * lbm_create_forest / lbm_plan_create, on the calling thread. */
+typedef int (*lbm_refine_fn)(int level, int bx, int by, int bz, void* user);
+typedef int (*lbm_flag_fn)(int level, double x, double y, double z, void* user);
+
+typedef struct lbm_forest lbm_forest;
+typedef struct lbm_plan lbm_plan;
+
+/* Thread-local text of the last failure on this thread ("" if none).  Never NULL. */
+const char* lbm_last_error(void);
+
+/* The D3Q19 tables in the order above: e[19][3], w[19], opposite index opp[19].  Host only. */
+lbm_status lbm_lattice(int32_t* e, double* w, int32_t* opp);
+
+/* ---- host-only forest planning (no CUDA call) -------------------------------------------
+ * Builds the leaf set (refinement by regions and callback, then 2:1 balance across faces,
+ * edges and corners, Sec. 3.2-3.3), the per-level block tables and the cell classes, without
+ * touching a GPU.  lbm_plan_leaves writes the level's leaf blocks as (bx, by, bz) triples in
+ * block-table order (pass NULL to query the count into *n).  lbm_plan_counts writes
+ * {leaf blocks, owned fluid cells, ghost-layer-1/2 fluid cells, ghost blocks}. */
+lbm_status lbm_plan_create(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag,
+                           void* user, lbm_plan** out);
+lbm_status lbm_plan_num_levels(const lbm_plan* p, int32_t* n_levels);
+lbm_status lbm_plan_leaves(const lbm_plan* p, int32_t level, int32_t* n, int32_t* blocks);
+lbm_status lbm_plan_counts(const lbm_plan* p, int32_t level, int64_t counts[4]);
+lbm_status lbm_plan_destroy(lbm_plan* p);
+
+/* ---- forest lifetime --------------------------------------------------------------------
+ * lbm_create_forest plans the forest (as lbm_plan_create), allocates both PDF grids of every
+ * level on the current CUDA device (two-grid storage, Sec. 4.1), uploads the block tables and
+ * binds `stream`.  The state starts undefined; call lbm_set_level_params and
+ * lbm_init_equilibrium before stepping.  lbm_destroy frees everything (NULL is a no-op). */
+lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag,
+                             void* user, void* stream, lbm_forest** out);
+lbm_status lbm_destroy(lbm_forest* f);
+lbm_status lbm_num_levels(const lbm_forest* f, int32_t* n_levels);
+
+/* Leaf blocks of `level` as (bx, by, bz) triples: the block-major order of every per-level
+ * array.  Pass blocks = NULL to query the count into *n. */
+lbm_status lbm_get_block_table(const lbm_forest* f, int32_t level, int32_t* n, int32_t* blocks);
+
+/* Cell updates of one coarse step: sum over levels of owned fluid cells x 2^L (every level
+ * L takes 2^L steps per coarse step, Sec. 2.3). */
+lbm_status lbm_cell_updates_per_coarse_step(const lbm_forest* f, int64_t* n);
+
+/* ---- parameters (Sec. 2.3) ----------------------------------------------------------------
+ * From the level-0 rate: lambda_e,L (or omega_L) by Eq. (omega_scaling_0), lambda_o,L by
+ * Eq. (lambda_oL) at fixed magic parameter Lambda_eo (ignored for SRT, where lambda_o =
+ * lambda_e), body acceleration a_L = a_0 / 2^L by Eq. (force_scaling).  accel0 may be NULL.
+ * The explicit variant takes per-level arrays lambda_e[n_levels], lambda_o[n_levels],
+ * accel[n_levels][3].  Both copy the values to the device on the forest's stream. */
+lbm_status lbm_set_level_params(lbm_forest* f, double lambda_e0, double magic_lambda,
+                                const double accel0[3]);
+lbm_status lbm_set_level_params_explicit(lbm_forest* f, const double* lambda_e,
+                                         const double* lambda_o, const double* accel);
+
+/* ---- state --------------------------------------------------------------------------------
+ * Equilibrium start (Eq. fequ) on one level: f = f^eq(rho, u) on owned fluid cells, taken
+ * as the post-streaming state of Fig. 5 (1).  rho[n_cells] and u[3][n_cells] are block-major
+ * FP64 arrays (n_cells = leaf blocks x B^3; values of obstacle cells are ignored); either may
+ * be NULL for rho0 / rest.  level = -1 applies rho = rho0, u = u_const to every level, with
+ * u_const given in `u` as 3 doubles (NULL = rest). */
+lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho, const double* u,
+                                int32_t on_device);
+
+/* Advances n_steps coarse time steps: Alg. 1 with the finer level's explosion reads, same-level
+ * exchange and coalescence fused into each level's stream-collide kernel (Alg. 2).  The whole
+ * coarse step is one CUDA graph, replayed per step on the forest's stream; asynchronous. */
+lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps);
+
+/* Macroscopic fields (Eq. fvelocity; the velocity adds a_L/2 as in Sec. 2.1) of the current
+ * state of one level, block-major FP64: rho[n_cells], u[3][n_cells]; NaN on obstacle cells.
+ * Either output may be NULL.  Synchronises the stream when on_device = 0. */
+lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double* u,
+                               int32_t on_device);
+
+/* PDFs of one level's owned cells, pdfs[19][n_cells] FP64 (unshifted f_a), block-major.  The
+ * stored state is the post-collision state of the next step (the kernels store f-tilde).
+ * lbm_set_pdfs writes the same layout back (checkpoint / resume, bit-exact for FP64). */
+lbm_status lbm_get_pdfs(lbm_forest* f, int32_t level, double* pdfs, int32_t on_device);
+lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_t on_device);
+
+/* Volume-weighted totals over owned fluid cells of all levels, FP64: out[0] = sum 8^-L rho,
+ * out[1..3] = sum 8^-L j with j = sum_a e_a f_a of the post-streaming state.  out is host
+ * memory; synchronises the stream.  Returns LBM_ENONFINITE if a total is not finite. */
+lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
+
+/* ---- measurement -------------------------------------------------------------------------
+ * lbm_timing_begin(f, max_steps) makes the next lbm_step_coarse calls (at most max_steps
+ * coarse steps in total) record CUDA events around every kernel of the captured graph, on the
+ * forest's stream.  lbm_timing_end synchronises and returns, per level, the summed kernel
+ * time in ms and the number of launches (arrays of length n_levels), then stops timing. */
+lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);
+lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level);
+
+/* Number of kernel launches one coarse step issues (the nodes of the captured graph). */
+lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,668 @@
+// C-ABI runtime: forest upload, level schedule, CUDA-graph replay, timing, reductions.
+//
+// The level schedule restates Alg. 1 with every collision fused into the preceding
+// stream (the kernels store post-collision states, Alg. 2's StreamCollide applied on all
+// levels).  Per coarse step, with F_L(s) the fused kernel of level L in its sub-step s:
+//     S(0) = [S(1)] F_0(1)          S(L) = [S(L+1)] F_L(1) [S(L+1)] F_L(2)   (L >= 1)
+// F_L(1) carries explosion (reads of the coarse post-collision parent for ghost layers),
+// stream, coalescence (reads of the finer ghost layers) and the second collision of Alg. 1;
+// F_L(2) carries the second stream and the first collision of the next visit.  Levels >= 1
+// flip their two-grid parity an even number of times per coarse step, level 0 once; the
+// runtime therefore captures one graph per level-0 parity and replays them alternately.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                              \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", #call,   \
+                        cudaGetErrorString(e_));                                                              \
+    } while (0)
+
+struct Launch {
+    int level, substep, grid;
+};
+
+struct DevBuf {
+    void* f[2] = {nullptr, nullptr};
+    uint8_t* cell = nullptr;
+    int32_t *nbr = nullptr, *parent = nullptr, *child = nullptr, *pos = nullptr, *gcells = nullptr;
+    uint8_t* kind = nullptr;
+};
+
+__global__ void reduce_final_kernel(const double* partial, int n, double* out) {
+    __shared__ double red[4][256];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = 0; k < 4; k++) s[k] += partial[4 * i + k];
+    for (int k = 0; k < 4; k++) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (int(threadIdx.x) < w)
+            for (int k = 0; k < 4; k++) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+const Launchers& launchers_for(int precision) {
+    if (precision == LBM_FP64) return launchers_f64();
+    if (precision == LBM_FP32S) return launchers_f32();
+    return launchers_f16();
+}
+
+size_t elem_size(int precision) { return precision == LBM_FP64 ? 8 : (precision == LBM_FP32S ? 4 : 2); }
+
+}  // namespace
+
+struct lbm_forest {
+    Plan plan;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    const Launchers* L = nullptr;
+    size_t esize = 0;
+    std::vector<DevBuf> buf;
+    std::vector<DevLevel> dl;
+    std::vector<LevelParams> hp;
+    LevelParams* d_params = nullptr;
+    double* d_wall = nullptr;
+    double* d_partial = nullptr;
+    std::vector<int> red_grid;
+    int red_total = 0;
+    double* d_out = nullptr;
+    double* h_out = nullptr;
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    int cur[LBM_MAX_LEVELS] = {};
+    unsigned init_mask = 0;
+    bool params_set = false;
+    std::vector<Launch> sched;
+    cudaGraph_t graph[2][2] = {};
+    cudaGraphExec_t exec[2][2] = {};
+    std::vector<cudaEvent_t> cap_events[2][2];
+    std::vector<cudaGraphNode_t> ev_nodes[2];
+    bool timing = false;
+    int tmax = 0, tused = 0;
+    std::vector<cudaEvent_t> tev;
+    int64_t updates = 0;
+};
+
+namespace {
+
+void free_graphs(lbm_forest* f) {
+    for (int t = 0; t < 2; t++)
+        for (int p = 0; p < 2; p++) {
+            if (f->exec[t][p]) cudaGraphExecDestroy(f->exec[t][p]);
+            if (f->graph[t][p]) cudaGraphDestroy(f->graph[t][p]);
+            f->exec[t][p] = nullptr;
+            f->graph[t][p] = nullptr;
+            for (cudaEvent_t e : f->cap_events[t][p]) cudaEventDestroy(e);
+            f->cap_events[t][p].clear();
+        }
+    f->ev_nodes[0].clear();
+    f->ev_nodes[1].clear();
+}
+
+void free_timing(lbm_forest* f) {
+    for (cudaEvent_t e : f->tev) cudaEventDestroy(e);
+    f->tev.clear();
+    f->timing = false;
+    f->tmax = f->tused = 0;
+}
+
+StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
+    StepArgs a{};
+    const int L = l.level, n = f->plan.nlev;
+    a.lv = f->dl[L];
+    if (L > 0) a.co = f->dl[L - 1];
+    if (L + 1 < n) a.fi = f->dl[L + 1];
+    a.cur = cur[L];
+    a.cur_c = L > 0 ? cur[L - 1] : 0;
+    a.cur_f = L + 1 < n ? cur[L + 1] : 0;
+    a.substep = l.substep;
+    a.LB = f->plan.LB;
+    a.per = (f->plan.per[0] ? 1 : 0) | (f->plan.per[1] ? 2 : 0) | (f->plan.per[2] ? 4 : 0);
+    a.params = f->d_params + L;
+    a.wall = f->d_wall;
+    a.rho0 = f->plan.d.rho0;
+    return a;
+}
+
+void build_schedule(lbm_forest* f) {
+    f->sched.clear();
+    const int n = f->plan.nlev, B3 = f->plan.B * f->plan.B * f->plan.B;
+    auto push = [&](int L, int s) {
+        const HostLevel& V = f->plan.lv[L];
+        int grid = V.nown * (B3 / 256) + int((V.gcells.size() + 255) / 256);
+        f->sched.push_back({L, s, grid});
+    };
+    std::function<void(int)> rec = [&](int L) {
+        if (L == 0) {
+            if (n > 1) rec(1);
+            push(0, 1);
+            return;
+        }
+        if (L + 1 < n) rec(L + 1);
+        push(L, 1);
+        if (L + 1 < n) rec(L + 1);
+        push(L, 2);
+    };
+    rec(0);
+}
+
+lbm_status capture(lbm_forest* f, int timed, int parity) {
+    int cur[LBM_MAX_LEVELS];
+    std::memcpy(cur, f->cur, sizeof cur);
+    cur[0] = parity;
+    std::vector<cudaEvent_t>& evs = f->cap_events[timed][parity];
+    if (timed) {
+        evs.resize(f->sched.size() + 1);
+        for (auto& e : evs) CU(cudaEventCreate(&e));
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal));
+    for (size_t k = 0; k < f->sched.size(); k++) {
+        const Launch& l = f->sched[k];
+        if (timed) cudaEventRecord(evs[k], f->cap);
+        StepArgs a = make_args(f, l, cur);
+        f->L->step(a, f->plan.d.collision, l.grid, f->cap);
+        cur[l.level] ^= 1;
+    }
+    if (timed) cudaEventRecord(evs.back(), f->cap);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(f->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LBM_ECUDA, "kernel launch during capture failed: %s", cudaGetErrorString(le));
+    }
+    if (ce != cudaSuccess) return fail(LBM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+    f->graph[timed][parity] = g;
+    CU(cudaGraphInstantiate(&f->exec[timed][parity], g, 0));
+    if (timed) {
+        size_t nn = 0;
+        CU(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CU(cudaGraphGetNodes(g, nodes.data(), &nn));
+        f->ev_nodes[parity].assign(evs.size(), nullptr);
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            CU(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t e;
+            CU(cudaGraphEventRecordNodeGetEvent(nd, &e));
+            for (size_t k = 0; k < evs.size(); k++)
+                if (evs[k] == e) f->ev_nodes[parity][k] = nd;
+        }
+        for (cudaGraphNode_t nd : f->ev_nodes[parity])
+            if (!nd) return fail(LBM_ECUDA, "timing event node missing from the captured graph");
+    }
+    return LBM_OK;
+}
+
+lbm_status ensure_stage(lbm_forest* f, size_t bytes) {
+    if (f->stage_bytes >= bytes) return LBM_OK;
+    if (f->d_stage) cudaFree(f->d_stage);
+    f->d_stage = nullptr;
+    f->stage_bytes = 0;
+    CU(cudaMalloc(&f->d_stage, bytes));
+    f->stage_bytes = bytes;
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status upload(T** dst, const std::vector<T>& v) {
+    *dst = nullptr;
+    if (v.empty()) return LBM_OK;
+    CU(cudaMalloc(reinterpret_cast<void**>(dst), v.size() * sizeof(T)));
+    CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+lbm_status check_level(const lbm_forest* f, int level) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    if (level < 0 || level >= f->plan.nlev) return fail(LBM_EINVAL, "level %d out of range [0, %d)", level, f->plan.nlev);
+    return LBM_OK;
+}
+
+int64_t owned_cells(const lbm_forest* f, int L) {
+    return int64_t(f->plan.lv[L].nown) * f->plan.B * f->plan.B * f->plan.B;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_lattice(int32_t* e, double* w, int32_t* opp) {
+    if (!e || !w || !opp) return fail(LBM_EINVAL, "NULL output");
+    for (int q = 0; q < Q; q++) {
+        e[3 * q] = EX[q];
+        e[3 * q + 1] = EY[q];
+        e[3 * q + 2] = EZ[q];
+        w[q] = weight(q);
+        opp[q] = OPP[q];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_create(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag, void* user,
+                           lbm_plan** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_plan* p = new (std::nothrow) lbm_plan;
+    if (!p) return fail(LBM_ENOMEM, "host allocation failed");
+    std::string err;
+    if (!build_plan(d, refine, flag, user, p->p, err)) {
+        delete p;
+        return fail(LBM_EINVAL, "%s", err.c_str());
+    }
+    *out = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_num_levels(const lbm_plan* p, int32_t* n) {
+    if (!p || !n) return fail(LBM_EINVAL, "NULL argument");
+    *n = p->p.nlev;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_leaves(const lbm_plan* p, int32_t level, int32_t* n, int32_t* blocks) {
+    if (!p || !n) return fail(LBM_EINVAL, "NULL argument");
+    if (level < 0 || level >= p->p.nlev) return fail(LBM_EINVAL, "level out of range");
+    const HostLevel& V = p->p.lv[level];
+    *n = V.nown;
+    if (blocks) std::memcpy(blocks, V.pos.data(), size_t(V.nown) * 3 * sizeof(int32_t));
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_counts(const lbm_plan* p, int32_t level, int64_t counts[4]) {
+    if (!p || !counts) return fail(LBM_EINVAL, "NULL argument");
+    if (level < 0 || level >= p->p.nlev) return fail(LBM_EINVAL, "level out of range");
+    const HostLevel& V = p->p.lv[level];
+    counts[0] = V.nown;
+    counts[1] = V.nfluid;
+    counts[2] = int64_t(V.gcells.size());
+    counts[3] = V.nghost;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_destroy(lbm_plan* p) {
+    delete p;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_forest* f) {
+    if (!f) return LBM_OK;
+    if (f->stream || f->cap) cudaStreamSynchronize(f->stream);
+    free_graphs(f);
+    free_timing(f);
+    for (DevBuf& b : f->buf) {
+        cudaFree(b.f[0]);
+        cudaFree(b.f[1]);
+        cudaFree(b.cell);
+        cudaFree(b.nbr);
+        cudaFree(b.parent);
+        cudaFree(b.child);
+        cudaFree(b.pos);
+        cudaFree(b.gcells);
+        cudaFree(b.kind);
+    }
+    cudaFree(f->d_params);
+    cudaFree(f->d_wall);
+    cudaFree(f->d_partial);
+    cudaFree(f->d_out);
+    cudaFree(f->d_stage);
+    if (f->h_out) cudaFreeHost(f->h_out);
+    if (f->cap) cudaStreamDestroy(f->cap);
+    delete f;
+    return LBM_OK;
+}
+
+lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag, void* user,
+                             void* stream, lbm_forest** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_forest* f = new (std::nothrow) lbm_forest;
+    if (!f) return fail(LBM_ENOMEM, "host allocation failed");
+    std::string err;
+    if (!build_plan(d, refine, flag, user, f->plan, err)) {
+        delete f;
+        return fail(LBM_EINVAL, "%s", err.c_str());
+    }
+    f->stream = static_cast<cudaStream_t>(stream);
+    f->L = &launchers_for(f->plan.d.precision);
+    f->esize = elem_size(f->plan.d.precision);
+    const Plan& P = f->plan;
+    const int B3 = P.B * P.B * P.B;
+    auto bail = [&](lbm_status s) {
+        std::string keep = g_err;
+        lbm_destroy(f);
+        g_err = keep;
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(LBM_ECUDA, "cannot create the capture stream (is a CUDA device present?)"));
+    f->buf.resize(P.nlev);
+    f->dl.resize(P.nlev);
+    for (int L = 0; L < P.nlev; L++) {
+        const HostLevel& V = P.lv[L];
+        DevBuf& b = f->buf[L];
+        const int64_t ncells = int64_t(V.nbricks()) * B3;
+        for (int k = 0; k < 2; k++)
+            if (ncells && cudaMalloc(&b.f[k], size_t(ncells) * Q * f->esize) != cudaSuccess)
+                return bail(fail(LBM_ENOMEM, "cannot allocate %lld bytes of PDFs on level %d",
+                                 (long long)(ncells * Q * f->esize), L));
+        lbm_status s;
+        if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
+            (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
+            (s = upload(&b.kind, V.kind)))
+            return bail(s);
+        DevLevel& g = f->dl[L];
+        g.f[0] = b.f[0];
+        g.f[1] = b.f[1];
+        g.cell = b.cell;
+        g.nbr = b.nbr;
+        g.parent = b.parent;
+        g.child = b.child;
+        g.pos = b.pos;
+        g.kind = b.kind;
+        g.gcells = b.gcells;
+        g.nown = V.nown;
+        g.nbricks = V.nbricks();
+        g.ngcells = int(V.gcells.size());
+        g.ncells = ncells;
+        for (int a = 0; a < 3; a++) g.N[a] = V.N[a];
+        f->updates += V.nfluid << L;
+    }
+    // wall terms 6 w_a rho0 (e_a . u_w) of velocity faces (velocity bounce-back)
+    std::vector<double> wall(6 * Q, 0.0);
+    for (int face = 0; face < 6; face++)
+        if (P.d.bc[face] == LBM_BC_VELOCITY)
+            for (int q = 0; q < Q; q++)
+                wall[face * Q + q] = 6.0 * weight(q) * P.d.rho0 *
+                                     (EX[q] * P.d.bc_velocity[face][0] + EY[q] * P.d.bc_velocity[face][1] +
+                                      EZ[q] * P.d.bc_velocity[face][2]);
+    lbm_status s;
+    if ((s = upload(&f->d_wall, wall))) return bail(s);
+    f->hp.assign(P.nlev, LevelParams{});
+    if (cudaMalloc(&f->d_params, sizeof(LevelParams) * P.nlev) != cudaSuccess)
+        return bail(fail(LBM_ENOMEM, "cannot allocate level parameters"));
+    // reduction scratch: a fixed number of CTAs per level, so totals are summed in a fixed order
+    f->red_grid.assign(P.nlev, 0);
+    for (int L = 0; L < P.nlev; L++) {
+        int64_t n = owned_cells(f, L);
+        f->red_grid[L] = int(std::min<int64_t>((n + 255) / 256, 1216));
+        f->red_total += f->red_grid[L];
+    }
+    if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
+        cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
+        return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
+    build_schedule(f);
+    *out = f;
+    return LBM_OK;
+}
+
+lbm_status lbm_num_levels(const lbm_forest* f, int32_t* n) {
+    if (!f || !n) return fail(LBM_EINVAL, "NULL argument");
+    *n = f->plan.nlev;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_block_table(const lbm_forest* f, int32_t level, int32_t* n, int32_t* blocks) {
+    lbm_status s = check_level(f, level);
+    if (s) return s;
+    if (!n) return fail(LBM_EINVAL, "n is NULL");
+    const HostLevel& V = f->plan.lv[level];
+    *n = V.nown;
+    if (blocks) std::memcpy(blocks, V.pos.data(), size_t(V.nown) * 3 * sizeof(int32_t));
+    return LBM_OK;
+}
+
+lbm_status lbm_cell_updates_per_coarse_step(const lbm_forest* f, int64_t* n) {
+    if (!f || !n) return fail(LBM_EINVAL, "NULL argument");
+    *n = f->updates;
+    return LBM_OK;
+}
+
+lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n) {
+    if (!f || !n) return fail(LBM_EINVAL, "NULL argument");
+    int c = 0;
+    for (const Launch& l : f->sched) c += l.grid > 0;
+    *n = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_level_params_explicit(lbm_forest* f, const double* le, const double* lo, const double* acc) {
+    if (!f || !le || !lo) return fail(LBM_EINVAL, "NULL argument");
+    const Plan& P = f->plan;
+    for (int L = 0; L < P.nlev; L++) {
+        if (!(le[L] > 0.0 && le[L] < 2.0) || !(lo[L] > 0.0 && lo[L] < 2.0))
+            return fail(LBM_EINVAL, "relaxation rates of level %d outside ]0,2[", L);
+        LevelParams& h = f->hp[L];
+        h.le = le[L];
+        h.lo = P.d.collision == LBM_TRT ? lo[L] : le[L];
+        for (int k = 0; k < 3; k++) h.acc[k] = acc ? acc[3 * L + k] : 0.0;
+        for (int q = 0; q < Q; q++)
+            h.force[q] = 3.0 * weight(q) * P.d.rho0 * (EX[q] * h.acc[0] + EY[q] * h.acc[1] + EZ[q] * h.acc[2]);
+    }
+    CU(cudaMemcpyAsync(f->d_params, f->hp.data(), sizeof(LevelParams) * P.nlev, cudaMemcpyHostToDevice, f->stream));
+    CU(cudaStreamSynchronize(f->stream));
+    f->params_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_level_params(lbm_forest* f, double le0, double magic, const double accel0[3]) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    const int n = f->plan.nlev;
+    std::vector<double> le(n), lo(n), acc(3 * n);
+    for (int L = 0; L < n; L++) {
+        le[L] = scale_rate(le0, L);
+        lo[L] = f->plan.d.collision == LBM_TRT ? lambda_odd(le[L], magic) : le[L];
+        for (int k = 0; k < 3; k++) acc[3 * L + k] = accel0 ? std::ldexp(accel0[k], -L) : 0.0;
+    }
+    return lbm_set_level_params_explicit(f, le.data(), lo.data(), acc.data());
+}
+
+lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho, const double* u, int32_t on_device) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    if (!f->params_set) return fail(LBM_EINVAL, "set the level parameters before initialising");
+    const Plan& P = f->plan;
+    if (level == -1) {
+        double uc[4] = {P.d.rho0, u ? u[0] : 0.0, u ? u[1] : 0.0, u ? u[2] : 0.0};
+        for (int L = 0; L < P.nlev; L++) {
+            f->cur[L] = 0;
+            f->L->init(f->dl[L], 0, P.LB, f->d_params + L, P.d.rho0, nullptr, nullptr, 1, uc, P.d.collision, f->stream);
+        }
+        CU(cudaGetLastError());
+        f->init_mask = (1u << P.nlev) - 1;
+        return LBM_OK;
+    }
+    lbm_status s = check_level(f, level);
+    if (s) return s;
+    const int64_t n = owned_cells(f, level);
+    const double *dr = rho, *du = u;
+    if (!on_device && n && (rho || u)) {
+        if ((s = ensure_stage(f, size_t(n) * 4 * sizeof(double)))) return s;
+        double* st = static_cast<double*>(f->d_stage);
+        if (rho) CU(cudaMemcpyAsync(st, rho, n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        if (u) CU(cudaMemcpyAsync(st + n, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        dr = rho ? st : nullptr;
+        du = u ? st + n : nullptr;
+    }
+    double uc[4] = {0, 0, 0, 0};
+    f->cur[level] = 0;
+    f->L->init(f->dl[level], 0, P.LB, f->d_params + level, P.d.rho0, dr, du, 0, uc, P.d.collision, f->stream);
+    CU(cudaGetLastError());
+    if (!on_device) CU(cudaStreamSynchronize(f->stream));
+    f->init_mask |= 1u << level;
+    return LBM_OK;
+}
+
+lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    if (n_steps < 0) return fail(LBM_EINVAL, "negative step count");
+    if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
+        return fail(LBM_EINVAL, "set the level parameters and initialise every level before stepping");
+    for (int i = 0; i < n_steps; i++) {
+        const int p = f->cur[0];
+        const int timed = f->timing && f->tused < f->tmax ? 1 : 0;
+        if (!f->exec[timed][p]) {
+            lbm_status s = capture(f, timed, p);
+            if (s) return s;
+        }
+        if (timed) {
+            const size_t ne = f->ev_nodes[p].size();
+            for (size_t k = 0; k < ne; k++)
+                CU(cudaGraphExecEventRecordNodeSetEvent(f->exec[1][p], f->ev_nodes[p][k], f->tev[f->tused * ne + k]));
+            f->tused++;
+        }
+        CU(cudaGraphLaunch(f->exec[timed][p], f->stream));
+        f->cur[0] ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double* u, int32_t on_device) {
+    lbm_status s = check_level(f, level);
+    if (s) return s;
+    const Plan& P = f->plan;
+    const int64_t n = owned_cells(f, level);
+    if (n == 0) return LBM_OK;
+    double *dr = rho, *du = u;
+    if (!on_device) {
+        if ((s = ensure_stage(f, size_t(n) * 4 * sizeof(double)))) return s;
+        double* st = static_cast<double*>(f->d_stage);
+        dr = rho ? st : nullptr;
+        du = u ? st + n : nullptr;
+    }
+    f->L->macro(f->dl[level], f->cur[level], P.LB, f->d_params + level, P.d.rho0, dr, du, f->stream);
+    CU(cudaGetLastError());
+    if (!on_device) {
+        if (rho) CU(cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+        if (u) CU(cudaMemcpyAsync(u, du, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+        CU(cudaStreamSynchronize(f->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_pdfs(lbm_forest* f, int32_t level, double* pdfs, int32_t on_device) {
+    lbm_status s = check_level(f, level);
+    if (s) return s;
+    if (!pdfs) return fail(LBM_EINVAL, "pdfs is NULL");
+    const int64_t n = owned_cells(f, level);
+    if (n == 0) return LBM_OK;
+    double* d = pdfs;
+    if (!on_device) {
+        if ((s = ensure_stage(f, size_t(n) * Q * sizeof(double)))) return s;
+        d = static_cast<double*>(f->d_stage);
+    }
+    f->L->get_pdfs(f->dl[level], f->cur[level], f->plan.LB, f->plan.d.rho0, d, f->stream);
+    CU(cudaGetLastError());
+    if (!on_device) {
+        CU(cudaMemcpyAsync(pdfs, d, n * Q * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+        CU(cudaStreamSynchronize(f->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_t on_device) {
+    lbm_status s = check_level(f, level);
+    if (s) return s;
+    if (!pdfs) return fail(LBM_EINVAL, "pdfs is NULL");
+    const int64_t n = owned_cells(f, level);
+    const double* d = pdfs;
+    if (!on_device && n) {
+        if ((s = ensure_stage(f, size_t(n) * Q * sizeof(double)))) return s;
+        CU(cudaMemcpyAsync(f->d_stage, pdfs, n * Q * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+        d = static_cast<const double*>(f->d_stage);
+    }
+    f->cur[level] = 0;
+    f->L->set_pdfs(f->dl[level], 0, f->plan.LB, f->plan.d.rho0, d, f->stream);
+    CU(cudaGetLastError());
+    if (!on_device) CU(cudaStreamSynchronize(f->stream));
+    f->init_mask |= 1u << level;
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
+    if (!f || !out) return fail(LBM_EINVAL, "NULL argument");
+    const Plan& P = f->plan;
+    int off = 0;
+    for (int L = 0; L < P.nlev; L++) {
+        f->L->reduce(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, std::ldexp(1.0, -3 * L),
+                     f->d_partial + 4 * off, f->red_grid[L], f->stream);
+        off += f->red_grid[L];
+    }
+    reduce_final_kernel<<<1, 256, 0, f->stream>>>(f->d_partial, f->red_total, f->d_out);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(f->h_out, f->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+    CU(cudaStreamSynchronize(f->stream));
+    for (int k = 0; k < 4; k++) out[k] = f->h_out[k];
+    for (int k = 0; k < 4; k++)
+        if (!std::isfinite(out[k])) return fail(LBM_ENONFINITE, "non-finite total (component %d)", k);
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps) {
+    if (!f || max_steps < 0) return fail(LBM_EINVAL, "invalid argument");
+    free_timing(f);
+    const size_t ne = f->sched.size() + 1;
+    f->tev.resize(size_t(max_steps) * ne);
+    for (auto& e : f->tev) CU(cudaEventCreate(&e));
+    f->tmax = max_steps;
+    f->tused = 0;
+    f->timing = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    CU(cudaStreamSynchronize(f->stream));
+    const int n = f->plan.nlev;
+    std::vector<double> ms(n, 0.0);
+    std::vector<int64_t> cnt(n, 0);
+    const size_t ne = f->sched.size() + 1;
+    for (int r = 0; r < f->tused; r++)
+        for (size_t k = 0; k + 1 < ne; k++) {
+            if (f->sched[k].grid <= 0) continue;
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, f->tev[r * ne + k], f->tev[r * ne + k + 1]));
+            ms[f->sched[k].level] += t;
+            cnt[f->sched[k].level] += 1;
+        }
+    for (int L = 0; L < n; L++) {
+        if (ms_per_level) ms_per_level[L] = ms[L];
+        if (launches_per_level) launches_per_level[L] = cnt[L];
+    }
+    free_timing(f);
+    return LBM_OK;
+}
+
+}  // extern "C"

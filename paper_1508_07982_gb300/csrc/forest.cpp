@@ -1,0 +1,354 @@
+// Host-side forest planning: leaf set, 2:1 balance, bricks, neighbour tables, cell classes.
+//
+// Sec. 3.2-3.3 of the paper: a uniform grid of root blocks, blocks split into 8 while the
+// application marks them, extra splits so that neighbouring leaves (across faces, edges
+// and corners) differ by at most one level, every leaf holding B^3 cells.  On top of the
+// leaf set this file derives what the GPU kernels need per level:
+//  - owned bricks (the level's leaves) and ghost bricks: block positions covered by the
+//    next coarser level that touch an owned brick; they hold the fine ghost layers of
+//    Sec. 4 (layers 1-2 are streamed, layers 3+ are read through the coarse parent);
+//  - a 27-entry neighbour table per brick (periodic axes wrap), parent links from ghost
+//    bricks to the coarse brick under them (explosion, Eq. ctof) and child links from owned
+//    bricks to the finer ghost bricks inside them (coalescence, Eq. ftoc);
+//  - a cell class per cell, with ghost cells taking the obstacle flag of the coarse cell that
+//    covers them, so fluid/obstacle marking agrees across the interface (Sec. 4.1).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr uint8_t ABSENT = 0, LEAF = 1, SPLIT = 2;
+constexpr int64_t kMaxBlockGrid = int64_t(1) << 26;
+
+struct Builder {
+    Plan& p;
+    lbm_refine_fn refine;
+    lbm_flag_fn flag;
+    void* user;
+
+    int64_t lin(int L, int x, int y, int z) const {
+        const int* n = p.lv[L].nb;
+        return (int64_t(z) * n[1] + y) * n[0] + x;
+    }
+    // Wraps block coordinates on periodic axes; false if outside a walled face.
+    bool wrap(int L, int b[3]) const {
+        for (int a = 0; a < 3; a++) {
+            int n = p.lv[L].nb[a];
+            if (p.per[a]) b[a] = ((b[a] % n) + n) % n;
+            else if (b[a] < 0 || b[a] >= n) return false;
+        }
+        return true;
+    }
+    uint8_t state(int L, int x, int y, int z) const { return p.st[L][lin(L, x, y, z)]; }
+
+    bool region_marks(int L, int x, int y, int z) const {
+        double e = double(p.B) / double(1 << L);
+        double lo[3] = {x * e, y * e, z * e}, hi[3] = {(x + 1) * e, (y + 1) * e, (z + 1) * e};
+        for (int r = 0; r < p.d.n_regions; r++) {
+            const double* g = p.d.regions[r];
+            if (L >= int(g[1])) continue;
+            if (int(g[0]) == 0) {
+                bool hit = true;
+                for (int a = 0; a < 3; a++) hit = hit && g[2 + a] < hi[a] && lo[a] < g[5 + a];
+                if (hit) return true;
+            } else {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; a++) {
+                    double c = g[2 + a];
+                    double t = c < lo[a] ? lo[a] - c : (c > hi[a] ? c - hi[a] : 0.0);
+                    d2 += t * t;
+                }
+                if (d2 < g[5] * g[5]) return true;
+            }
+        }
+        return false;
+    }
+
+    void split(int L, int x, int y, int z) {
+        p.st[L][lin(L, x, y, z)] = SPLIT;
+        for (int c = 0; c < 8; c++)
+            p.st[L + 1][lin(L + 1, 2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + (c >> 2))] = LEAF;
+    }
+
+    // A leaf of level L is unbalanced when a split block of level L+1 touches it.
+    bool unbalanced(int L, int x, int y, int z) const {
+        for (int k = 2 * z - 1; k <= 2 * z + 2; k++)
+            for (int j = 2 * y - 1; j <= 2 * y + 2; j++)
+                for (int i = 2 * x - 1; i <= 2 * x + 2; i++) {
+                    int b[3] = {i, j, k};
+                    if (!wrap(L + 1, b)) continue;
+                    if (state(L + 1, b[0], b[1], b[2]) == SPLIT) return true;
+                }
+        return false;
+    }
+
+    bool leaves(std::string& err) {
+        int lmax = p.d.max_level;
+        p.st.assign(lmax + 1, {});
+        p.lv.assign(lmax + 1, HostLevel{});
+        for (int L = 0; L <= lmax; L++) {
+            int64_t n = 1;
+            for (int a = 0; a < 3; a++) {
+                p.lv[L].nb[a] = p.d.root_blocks[a] << L;
+                p.lv[L].N[a] = p.lv[L].nb[a] * p.B;
+                n *= p.lv[L].nb[a];
+            }
+            if (n > kMaxBlockGrid) {
+                err = "block grid of a level exceeds 2^26 positions";
+                return false;
+            }
+            p.st[L].assign(size_t(n), ABSENT);
+        }
+        std::fill(p.st[0].begin(), p.st[0].end(), LEAF);
+        for (bool changed = true; changed;) {
+            changed = false;
+            for (int L = 0; L < lmax; L++)
+                for (int z = 0; z < p.lv[L].nb[2]; z++)
+                    for (int y = 0; y < p.lv[L].nb[1]; y++)
+                        for (int x = 0; x < p.lv[L].nb[0]; x++) {
+                            if (state(L, x, y, z) != LEAF) continue;
+                            bool want = region_marks(L, x, y, z);
+                            if (!want && refine) want = refine(L, x, y, z, user) != 0;
+                            if (want) {
+                                split(L, x, y, z);
+                                changed = true;
+                            }
+                        }
+            for (int L = 0; L < lmax; L++)
+                for (int z = 0; z < p.lv[L].nb[2]; z++)
+                    for (int y = 0; y < p.lv[L].nb[1]; y++)
+                        for (int x = 0; x < p.lv[L].nb[0]; x++) {
+                            if (state(L, x, y, z) != LEAF) continue;
+                            if (unbalanced(L, x, y, z)) {
+                                split(L, x, y, z);
+                                changed = true;
+                            }
+                        }
+        }
+        p.nlev = 1;
+        for (int L = 0; L <= lmax; L++)
+            if (std::find(p.st[L].begin(), p.st[L].end(), LEAF) != p.st[L].end()) p.nlev = L + 1;
+        p.st.resize(p.nlev);
+        p.lv.resize(p.nlev);
+        return true;
+    }
+
+    bool obstacle(int L, int gx, int gy, int gz) const {
+        double s = 1.0 / double(1 << L);
+        double c[3] = {(gx + 0.5) * s, (gy + 0.5) * s, (gz + 0.5) * s};
+        for (int i = 0; i < p.d.n_spheres; i++) {
+            const double* q = p.d.spheres[i];
+            double d2 = (c[0] - q[0]) * (c[0] - q[0]) + (c[1] - q[1]) * (c[1] - q[1]) + (c[2] - q[2]) * (c[2] - q[2]);
+            if (d2 < q[3] * q[3]) return true;
+        }
+        return flag && flag(L, c[0], c[1], c[2], user) != 0;
+    }
+
+    bool bricks(int L, std::string& err) {
+        HostLevel& V = p.lv[L];
+        const int B = p.B, B3 = B * B * B;
+        const int64_t ngrid = int64_t(V.nb[0]) * V.nb[1] * V.nb[2];
+        std::vector<int32_t> index(size_t(ngrid), -1);
+        // owned bricks: the leaves of this level, x fastest
+        for (int z = 0; z < V.nb[2]; z++)
+            for (int y = 0; y < V.nb[1]; y++)
+                for (int x = 0; x < V.nb[0]; x++)
+                    if (state(L, x, y, z) == LEAF) {
+                        index[lin(L, x, y, z)] = int32_t(V.pos.size() / 3);
+                        V.pos.insert(V.pos.end(), {x, y, z});
+                    }
+        V.nown = int(V.pos.size() / 3);
+        // ghost bricks: coarser-covered positions touching an owned brick
+        if (L > 0) {
+            for (int z = 0; z < V.nb[2]; z++)
+                for (int y = 0; y < V.nb[1]; y++)
+                    for (int x = 0; x < V.nb[0]; x++) {
+                        if (state(L, x, y, z) != ABSENT) continue;
+                        bool touch = false;
+                        for (int o = 0; o < 27 && !touch; o++) {
+                            int b[3] = {x + o % 3 - 1, y + (o / 3) % 3 - 1, z + o / 9 - 1};
+                            if (o == 13 || !wrap(L, b)) continue;
+                            int32_t k = index[lin(L, b[0], b[1], b[2])];
+                            touch = k >= 0 && k < V.nown;
+                        }
+                        if (!touch) continue;
+                        if (state(L - 1, x >> 1, y >> 1, z >> 1) != LEAF) {
+                            err = "a block next to a leaf is covered by a leaf two levels coarser";
+                            return false;
+                        }
+                        index[lin(L, x, y, z)] = int32_t(V.pos.size() / 3);
+                        V.pos.insert(V.pos.end(), {x, y, z});
+                    }
+        }
+        const int nbk = int(V.pos.size() / 3);
+        V.nghost = nbk - V.nown;
+        V.nbr.assign(size_t(nbk) * 27, NB_COARSE);
+        V.kind.assign(size_t(nbk), 0);
+        V.parent.assign(size_t(nbk), -1);
+        for (int k = 0; k < nbk; k++) {
+            const int* P = &V.pos[3 * k];
+            for (int o = 0; o < 27; o++) {
+                int b[3] = {P[0] + o % 3 - 1, P[1] + (o / 3) % 3 - 1, P[2] + o / 9 - 1};
+                int32_t v;
+                if (!wrap(L, b)) v = NB_WALL;
+                else {
+                    int32_t idx = index[lin(L, b[0], b[1], b[2])];
+                    if (idx >= 0) v = idx;
+                    else if (state(L, b[0], b[1], b[2]) == SPLIT) v = NB_FINER;
+                    else v = NB_COARSE;
+                }
+                V.nbr[size_t(k) * 27 + o] = v;
+                if (v == NB_FINER) V.kind[k] |= BK_TOUCH_FINER;
+            }
+            if (k >= V.nown) {
+                V.kind[k] |= BK_GHOST;
+                const HostLevel& C = p.lv[L - 1];
+                int32_t pb = -1;
+                // the coarse brick under this ghost brick is an owned brick of level L-1
+                for (int c = 0; c < C.nown; c++)
+                    if (C.pos[3 * c] == P[0] >> 1 && C.pos[3 * c + 1] == P[1] >> 1 && C.pos[3 * c + 2] == P[2] >> 1) {
+                        pb = c;
+                        break;
+                    }
+                if (pb < 0) {
+                    err = "ghost brick without a coarse parent brick";
+                    return false;
+                }
+                V.parent[k] = pb * 8 + ((P[0] & 1) | ((P[1] & 1) << 1) | ((P[2] & 1) << 2));
+            }
+        }
+        // cell classes
+        V.cell.assign(size_t(nbk) * B3, CK_FLUID);
+        for (int k = 0; k < nbk; k++) {
+            const int* P = &V.pos[3 * k];
+            uint8_t* cells = &V.cell[size_t(k) * B3];
+            if (k < V.nown) {
+                bool pure = true;
+                for (int z = 0; z < B; z++)
+                    for (int y = 0; y < B; y++)
+                        for (int x = 0; x < B; x++)
+                            if (obstacle(L, P[0] * B + x, P[1] * B + y, P[2] * B + z)) {
+                                cells[(z * B + y) * B + x] = CK_SOLID;
+                                pure = false;
+                            } else {
+                                V.nfluid++;
+                            }
+                if (pure) V.kind[k] |= BK_PURE;
+                continue;
+            }
+            for (int z = 0; z < B; z++)
+                for (int y = 0; y < B; y++)
+                    for (int x = 0; x < B; x++) {
+                        int l[3] = {x, y, z};
+                        int dmin = 1 << 20;
+                        for (int o = 0; o < 27; o++) {
+                            int32_t nk = V.nbr[size_t(k) * 27 + o];
+                            if (o == 13 || nk < 0 || nk >= V.nown) continue;
+                            int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+                            int d = 0;
+                            for (int a = 0; a < 3; a++) {
+                                int da = off[a] == 0 ? 0 : (off[a] > 0 ? B - l[a] : l[a] + 1);
+                                d = std::max(d, da);
+                            }
+                            dmin = std::min(dmin, d);
+                        }
+                        int g[3] = {P[0] * B + x, P[1] * B + y, P[2] * B + z};
+                        uint8_t ck;
+                        if (obstacle(L - 1, g[0] >> 1, g[1] >> 1, g[2] >> 1)) ck = CK_SOLID;
+                        else ck = dmin <= 2 ? CK_GHOST : CK_FAR;
+                        int c = (z * B + y) * B + x;
+                        cells[c] = ck;
+                        if (ck == CK_GHOST) V.gcells.push_back(int32_t(size_t(k) * B3 + c));
+                    }
+        }
+        return true;
+    }
+
+    void children(int L) {
+        HostLevel& V = p.lv[L];
+        V.child.assign(size_t(V.nown) * 8, -1);
+        if (L + 1 >= p.nlev) return;
+        const HostLevel& F = p.lv[L + 1];
+        for (int g = F.nown; g < F.nbricks(); g++) {
+            const int* P = &F.pos[3 * g];
+            int pb = F.parent[g] >> 3, oct = F.parent[g] & 7;
+            (void)P;
+            V.child[size_t(pb) * 8 + oct] = g;
+        }
+    }
+};
+
+}  // namespace
+
+double scale_rate(double w0, int L) {
+    double p2 = std::ldexp(1.0, L);
+    return 2.0 * w0 / (2.0 * p2 + (1.0 - p2) * w0);
+}
+
+double lambda_odd(double le, double magic) { return (4.0 - 2.0 * le) / (2.0 + (4.0 * magic - 1.0) * le); }
+
+bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag, void* user, Plan& p,
+                std::string& err) {
+    if (!d) {
+        err = "description is NULL";
+        return false;
+    }
+    p.d = *d;
+    int B = d->block_cells;
+    if (B != 8 && B != 16 && B != 32) {
+        err = "block_cells must be 8, 16 or 32";
+        return false;
+    }
+    p.B = B;
+    p.LB = B == 8 ? 3 : (B == 16 ? 4 : 5);
+    if (d->max_level < 0 || d->max_level >= LBM_MAX_LEVELS) {
+        err = "max_level out of range";
+        return false;
+    }
+    if (d->n_spheres < 0 || d->n_spheres > LBM_MAX_SPHERES || d->n_regions < 0 || d->n_regions > LBM_MAX_REGIONS) {
+        err = "too many spheres or regions";
+        return false;
+    }
+    if (d->precision < LBM_FP64 || d->precision > LBM_FP16S || d->collision < LBM_SRT || d->collision > LBM_TRT) {
+        err = "unknown precision or collision model";
+        return false;
+    }
+    if (!(d->rho0 > 0.0)) {
+        err = "rho0 must be positive";
+        return false;
+    }
+    for (int a = 0; a < 3; a++) {
+        if (d->root_blocks[a] < 1 || d->root_blocks[a] > 4096) {
+            err = "root_blocks out of range";
+            return false;
+        }
+        for (int s = 0; s < 2; s++)
+            if (d->bc[2 * a + s] < LBM_BC_PERIODIC || d->bc[2 * a + s] > LBM_BC_VELOCITY) {
+                err = "unknown boundary condition";
+                return false;
+            }
+        bool p0 = d->bc[2 * a] == LBM_BC_PERIODIC, p1 = d->bc[2 * a + 1] == LBM_BC_PERIODIC;
+        if (p0 != p1) {
+            err = "periodic faces must come in pairs";
+            return false;
+        }
+        p.per[a] = p0;
+        if ((int64_t(d->root_blocks[a]) * B) << d->max_level >= (int64_t(1) << 30)) {
+            err = "domain too large";
+            return false;
+        }
+    }
+    Builder b{p, refine, flag, user};
+    if (!b.leaves(err)) return false;
+    for (int L = 0; L < p.nlev; L++)
+        if (!b.bricks(L, err)) return false;
+    for (int L = 0; L < p.nlev; L++) b.children(L);
+    return true;
+}
+
+}  // namespace lbm

@@ -1,0 +1,60 @@
+// Structures shared between the host runtime (capi.cu) and the kernels, and the launchers that
+// each per-precision translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Per-level parameters, device-resident so that captured graphs never need rebuilding.
+struct LevelParams {
+    double le, lo;        // lambda_e, lambda_o (omega, omega for SRT)
+    double force[19];     // 3 w_a rho0 (e_a . a_L)
+    double acc[3];        // a_L
+};
+
+struct DevLevel {
+    void* f[2];           // two PDF grids, [19][ncells]
+    const uint8_t* cell;  // [ncells] CK_*
+    const int32_t* nbr;   // [nbricks][27]
+    const int32_t* parent;
+    const int32_t* child;
+    const int32_t* pos;   // [nbricks][3]
+    const uint8_t* kind;  // [nbricks]
+    const int32_t* gcells;
+    int nown, nbricks, ngcells;
+    int64_t ncells;
+    int N[3];
+};
+
+struct StepArgs {
+    DevLevel lv, co, fi;  // this level, the next coarser, the next finer
+    int cur, cur_c, cur_f;
+    int substep;          // 1: ghost layers hold exploded values; 2: they hold sub-step-1 values
+    int LB;
+    int per;              // bit a set: axis a periodic
+    const LevelParams* params;
+    const double* wall;   // [6][19] 6 w_a rho0 (e_a . u_w) per face
+    double rho0;
+};
+
+// Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).
+struct Launchers {
+    void (*step)(const StepArgs& a, int collision, int grid, cudaStream_t s);
+    void (*init)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, const double* rho,
+                 const double* u, int uniform, const double u_const[4], int collision, cudaStream_t s);
+    void (*macro)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double* rho, double* u,
+                  cudaStream_t s);
+    void (*get_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, double* out, cudaStream_t s);
+    void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
+    void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
+                   int grid, cudaStream_t s);
+};
+const Launchers& launchers_f64();
+const Launchers& launchers_f32();
+const Launchers& launchers_f16();
+
+}  // namespace lbm

@@ -1,0 +1,49 @@
+// Launcher definitions for one storage type; included once per precision translation unit.
+#pragma once
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+template <typename T, typename C>
+struct LaunchImpl {
+    static void step(const StepArgs& a, int collision, int grid, cudaStream_t s) {
+        if (grid <= 0) return;
+        if (collision == LBM_TRT) step_kernel<T, C, LBM_TRT><<<grid, 256, 0, s>>>(a);
+        else step_kernel<T, C, LBM_SRT><<<grid, 256, 0, s>>>(a);
+    }
+    static void init(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, const double* rho,
+                     const double* u, int uniform, const double uc[4], int collision, cudaStream_t s) {
+        if (lv.ncells == 0) return;
+        const int grid = int((lv.ncells + 255) / 256);
+        if (collision == LBM_TRT)
+            init_kernel<T, C, LBM_TRT><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u, uniform, uc[0], uc[1], uc[2], uc[3]);
+        else
+            init_kernel<T, C, LBM_SRT><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u, uniform, uc[0], uc[1], uc[2], uc[3]);
+    }
+    static void macro(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double* rho, double* u,
+                      cudaStream_t s) {
+        const int64_t n = int64_t(lv.nown) << (3 * LB);
+        if (n == 0) return;
+        macro_kernel<T><<<int((n + 255) / 256), 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u);
+    }
+    static void get_pdfs(const DevLevel& lv, int cur, int LB, double rho0, double* out, cudaStream_t s) {
+        const int64_t n = int64_t(lv.nown) << (3 * LB);
+        if (n == 0) return;
+        get_pdfs_kernel<T><<<int((n + 255) / 256), 256, 0, s>>>(lv, cur, LB, rho0, out);
+    }
+    static void set_pdfs(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s) {
+        if (lv.ncells == 0) return;
+        set_pdfs_kernel<T><<<int((lv.ncells + 255) / 256), 256, 0, s>>>(lv, cur, LB, rho0, in);
+    }
+    static void reduce(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w,
+                       double* partial, int grid, cudaStream_t s) {
+        if (grid <= 0) return;
+        reduce_level_kernel<T><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, w, partial);
+    }
+    static const Launchers& get() {
+        static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce};
+        return L;
+    }
+};
+
+}  // namespace lbm

@@ -1,0 +1,347 @@
+"""Thin ctypes binding of the C-ABI in ``include/lbm_gb300.h``.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  The shared library is the in-tree ``_lib/liblbm_gb300.so`` built by
+``build.py``; importing this module fails loudly if it is missing.  PyTorch is
+used for device buffers and streams (tensors are passed by ``data_ptr()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+Q = 19
+
+LBM_OK, LBM_EINVAL, LBM_EUNBALANCED, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENONFINITE = range(7)
+PRECISION = {"fp64": 0, "fp32s": 1, "fp16s": 2}
+_BC = {"periodic": 0, "noslip": 1, "velocity": 2}
+_COLL = {"srt": 0, "trt": 1}
+
+# Every entry point of include/lbm_gb300.h (checked by the tests).
+EXPORTS = [
+    "lbm_last_error", "lbm_lattice", "lbm_plan_create", "lbm_plan_num_levels", "lbm_plan_leaves",
+    "lbm_plan_counts", "lbm_plan_destroy", "lbm_create_forest", "lbm_destroy", "lbm_num_levels",
+    "lbm_get_block_table", "lbm_cell_updates_per_coarse_step", "lbm_set_level_params",
+    "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
+    "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
+    "lbm_launches_per_coarse_step",
+]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("root_blocks", ctypes.c_int32 * 3),
+        ("block_cells", ctypes.c_int32),
+        ("max_level", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 6),
+        ("bc_velocity", (ctypes.c_double * 3) * 6),
+        ("rho0", ctypes.c_double),
+        ("n_spheres", ctypes.c_int32),
+        ("spheres", (ctypes.c_double * 4) * 64),
+        ("n_regions", ctypes.c_int32),
+        ("regions", (ctypes.c_double * 8) * 64),
+    ]
+
+
+REFINE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p)
+FLAG_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_void_p)
+
+_lib = None
+
+
+def library():
+    """Loads the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("CUDA library %s is missing: run __graft_entry__.build() first" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.lbm_last_error.restype = ctypes.c_char_p
+        sig = {
+            "lbm_lattice": [i32p, dp, i32p],
+            "lbm_plan_create": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, ctypes.POINTER(P)],
+            "lbm_plan_num_levels": [P, i32p],
+            "lbm_plan_leaves": [P, ctypes.c_int32, i32p, i32p],
+            "lbm_plan_counts": [P, ctypes.c_int32, i64p],
+            "lbm_plan_destroy": [P],
+            "lbm_create_forest": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, P, ctypes.POINTER(P)],
+            "lbm_destroy": [P],
+            "lbm_num_levels": [P, i32p],
+            "lbm_get_block_table": [P, ctypes.c_int32, i32p, i32p],
+            "lbm_cell_updates_per_coarse_step": [P, i64p],
+            "lbm_set_level_params": [P, ctypes.c_double, ctypes.c_double, dp],
+            "lbm_set_level_params_explicit": [P, dp, dp, dp],
+            "lbm_init_equilibrium": [P, ctypes.c_int32, P, P, ctypes.c_int32],
+            "lbm_step_coarse": [P, ctypes.c_int32],
+            "lbm_get_macroscopic": [P, ctypes.c_int32, P, P, ctypes.c_int32],
+            "lbm_get_pdfs": [P, ctypes.c_int32, P, ctypes.c_int32],
+            "lbm_set_pdfs": [P, ctypes.c_int32, P, ctypes.c_int32],
+            "lbm_reduce_mass_momentum": [P, dp],
+            "lbm_timing_begin": [P, ctypes.c_int32],
+            "lbm_timing_end": [P, dp, i64p],
+            "lbm_launches_per_coarse_step": [P, i32p],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != LBM_OK:
+        raise LBMError(status, library().lbm_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(x):
+    """Pointer of a numpy array (host) or a torch tensor (host or device); None stays NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def lbm_lattice():
+    e = np.zeros((Q, 3), np.int32)
+    w = np.zeros(Q)
+    opp = np.zeros(Q, np.int32)
+    _check(library().lbm_lattice(e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(w),
+                                 opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return e, w, opp
+
+
+def make_desc(case, precision="fp64"):
+    """Marshals a case dict (keys documented in inputs.py) into lbm_forest_desc."""
+    d = Desc()
+    for a in range(3):
+        d.root_blocks[a] = int(case["root"][a])
+    d.block_cells = int(case["B"])
+    d.max_level = int(case.get("lmax", 0))
+    d.precision = PRECISION[precision]
+    d.collision = _COLL[case.get("collision", "trt")]
+    bcs = case.get("bc", ["periodic"] * 6)
+    bcu = case.get("bc_u", [(0.0, 0.0, 0.0)] * 6)
+    for k in range(6):
+        d.bc[k] = _BC[bcs[k]]
+        for a in range(3):
+            d.bc_velocity[k][a] = float(bcu[k][a])
+    d.rho0 = float(case.get("rho0", 1.0))
+    sph = case.get("spheres", [])
+    d.n_spheres = len(sph)
+    for i, s in enumerate(sph):
+        for a in range(4):
+            d.spheres[i][a] = float(s[a])
+    reg = case.get("regions", [])
+    d.n_regions = len(reg)
+    for i, r in enumerate(reg):
+        if r[0] == "box":
+            vals = [0.0, float(r[1])] + [float(v) for v in r[2]] + [float(v) for v in r[3]]
+        else:
+            vals = [1.0, float(r[1])] + [float(v) for v in r[2]] + [float(r[3]), 0.0, 0.0]
+        for k in range(8):
+            d.regions[i][k] = vals[k]
+    return d
+
+
+class Plan:
+    """Host-only forest plan (lbm_plan_*): leaf set and per-level counts, no GPU needed."""
+
+    def __init__(self, case, refine=None, flag=None):
+        L = library()
+        self._refine = REFINE_FN(refine) if refine else REFINE_FN()
+        self._flag = FLAG_FN(flag) if flag else FLAG_FN()
+        self._d = make_desc(case)
+        h = ctypes.c_void_p()
+        _check(L.lbm_plan_create(ctypes.byref(self._d), self._refine, self._flag, None, ctypes.byref(h)))
+        self.h = h
+        n = ctypes.c_int32()
+        _check(L.lbm_plan_num_levels(self.h, ctypes.byref(n)))
+        self.nlev = n.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            library().lbm_plan_destroy(self.h)
+            self.h = None
+
+    def leaves(self, level):
+        n = ctypes.c_int32()
+        _check(library().lbm_plan_leaves(self.h, level, ctypes.byref(n), None))
+        out = np.zeros((max(n.value, 1), 3), np.int32)
+        _check(library().lbm_plan_leaves(self.h, level, ctypes.byref(n), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out[:n.value]
+
+    def counts(self, level):
+        c = np.zeros(4, np.int64)
+        _check(library().lbm_plan_counts(self.h, level, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return dict(blocks=int(c[0]), fluid=int(c[1]), ghost12=int(c[2]), ghost_blocks=int(c[3]))
+
+
+class Forest:
+    """A refined-grid simulation on the current CUDA device (lbm_create_forest ... lbm_destroy)."""
+
+    def __init__(self, case, precision="fp64", refine=None, flag=None, stream=None):
+        L = library()
+        self.case = case
+        self.precision = precision
+        self._refine = REFINE_FN(refine) if refine else REFINE_FN()
+        self._flag = FLAG_FN(flag) if flag else FLAG_FN()
+        self._d = make_desc(case, precision)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        _check(L.lbm_create_forest(ctypes.byref(self._d), self._refine, self._flag, None,
+                                   ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.h = h
+        n = ctypes.c_int32()
+        _check(L.lbm_num_levels(self.h, ctypes.byref(n)))
+        self.nlev = n.value
+        self.B = int(case["B"])
+        if "lambda_e0" in case:
+            self.set_level_params(case["lambda_e0"], case.get("magic", 3.0 / 16.0), case.get("accel", (0.0, 0.0, 0.0)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(library().lbm_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- tables
+    def block_table(self, level):
+        n = ctypes.c_int32()
+        _check(library().lbm_get_block_table(self.h, level, ctypes.byref(n), None))
+        out = np.zeros((max(n.value, 1), 3), np.int32)
+        _check(library().lbm_get_block_table(self.h, level, ctypes.byref(n),
+                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out[:n.value]
+
+    def n_cells(self, level):
+        return len(self.block_table(level)) * self.B ** 3
+
+    def cell_coords(self, level):
+        """Global level coordinates (X, Y, Z) of the block-major cell order, each [n_cells]."""
+        bt = self.block_table(level)
+        B = self.B
+        r = np.arange(B)
+        lz, ly, lx = np.meshgrid(r, r, r, indexing="ij")
+        X = (bt[:, 0:1] * B + lx.reshape(1, -1)).reshape(-1)
+        Y = (bt[:, 1:2] * B + ly.reshape(1, -1)).reshape(-1)
+        Z = (bt[:, 2:3] * B + lz.reshape(1, -1)).reshape(-1)
+        return X, Y, Z
+
+    def cell_updates_per_coarse_step(self):
+        n = ctypes.c_int64()
+        _check(library().lbm_cell_updates_per_coarse_step(self.h, ctypes.byref(n)))
+        return n.value
+
+    def launches_per_coarse_step(self):
+        n = ctypes.c_int32()
+        _check(library().lbm_launches_per_coarse_step(self.h, ctypes.byref(n)))
+        return n.value
+
+    # -- parameters and state
+    def set_level_params(self, lambda_e0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0)):
+        a = np.ascontiguousarray(accel, dtype=np.float64)
+        _check(library().lbm_set_level_params(self.h, lambda_e0, magic, _dp(a)))
+
+    def set_level_params_explicit(self, le, lo, acc):
+        le = np.ascontiguousarray(le, dtype=np.float64)
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        acc = np.ascontiguousarray(acc, dtype=np.float64).reshape(-1)
+        _check(library().lbm_set_level_params_explicit(self.h, _dp(le), _dp(lo), _dp(acc)))
+
+    def init_equilibrium(self, level, rho=None, u=None, on_device=False):
+        keep = []
+        if not on_device:
+            if rho is not None:
+                rho = np.ascontiguousarray(rho, dtype=np.float64)
+                keep.append(rho)
+            if u is not None:
+                u = np.ascontiguousarray(u, dtype=np.float64)
+                keep.append(u)
+        _check(library().lbm_init_equilibrium(self.h, level, _ptr(rho), _ptr(u), 1 if on_device else 0))
+
+    def init_uniform(self, u=(0.0, 0.0, 0.0)):
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        _check(library().lbm_init_equilibrium(self.h, -1, None, uu.ctypes.data, 0))
+
+    def init_fields(self, field):
+        """f^eq from field(level, X, Y, Z) -> (rho, (ux, uy, uz)) on every level."""
+        for L in range(self.nlev):
+            X, Y, Z = self.cell_coords(L)
+            if X.size == 0:
+                self.init_equilibrium(L)
+                continue
+            rho, u = field(L, X, Y, Z)
+            rho = np.broadcast_to(np.asarray(rho, np.float64), X.shape)
+            u = np.stack([np.broadcast_to(np.asarray(c, np.float64), X.shape) for c in u])
+            self.init_equilibrium(L, rho, u)
+
+    def step_coarse(self, n=1):
+        _check(library().lbm_step_coarse(self.h, n))
+
+    def get_macroscopic(self, level, rho=None, u=None, on_device=False):
+        if on_device:
+            _check(library().lbm_get_macroscopic(self.h, level, _ptr(rho), _ptr(u), 1))
+            return rho, u
+        n = self.n_cells(level)
+        rho = np.zeros(n)
+        u = np.zeros((3, n))
+        _check(library().lbm_get_macroscopic(self.h, level, rho.ctypes.data, u.ctypes.data, 0))
+        return rho, u
+
+    def get_pdfs(self, level, out=None, on_device=False):
+        if on_device:
+            _check(library().lbm_get_pdfs(self.h, level, _ptr(out), 1))
+            return out
+        n = self.n_cells(level)
+        out = np.zeros((Q, n))
+        if n:
+            _check(library().lbm_get_pdfs(self.h, level, out.ctypes.data, 0))
+        return out
+
+    def set_pdfs(self, level, pdfs, on_device=False):
+        if not on_device:
+            pdfs = np.ascontiguousarray(pdfs, dtype=np.float64)
+        _check(library().lbm_set_pdfs(self.h, level, _ptr(pdfs), 1 if on_device else 0))
+
+    def reduce_mass_momentum(self):
+        out = np.zeros(4)
+        _check(library().lbm_reduce_mass_momentum(self.h, _dp(out)))
+        return out
+
+    def timing_begin(self, max_steps):
+        _check(library().lbm_timing_begin(self.h, max_steps))
+
+    def timing_end(self):
+        ms = np.zeros(self.nlev)
+        cnt = np.zeros(self.nlev, np.int64)
+        _check(library().lbm_timing_end(self.h, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return ms, cnt

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle, element by element.
+
+The kernels store the post-collision state, so the GPU PDFs after n coarse steps are compared
+with the oracle's state after n coarse steps plus one more collision (orc_get_f with
+post_collision).  FP64 tolerance: relative max-norm 1e-12 over owned fluid cells of all levels
+(FMA and summation order differ from the oracle; no bitwise equality is claimed).  Integer
+results (block tables, which cells are fluid) must agree exactly.
+"""
+import numpy as np
+import pytest
+
+from paper_1508_07982_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07982_gb300 import build, lbm as mod
+    build.build()
+    return mod
+
+
+def _compare(f, o, post_collision=True):
+    """max |f_gpu - f_oracle| / max |f_oracle| over owned fluid cells; also checks that exactly the
+    oracle's non-fluid owned cells come back as NaN."""
+    num, den = 0.0, 0.0
+    for L in range(f.nlev):
+        g = f.get_pdfs(L)
+        X, Y, Z = f.cell_coords(L)
+        if X.size == 0:
+            continue
+        idx = o.lookup(L, X, Y, Z)
+        cls, flg = o.classes(L)
+        fluid = (cls[idx] == 1) & (flg[idx] == 0)
+        assert (cls[idx] == 1).all()
+        ref = o.get_f(L, post_collision=post_collision)[idx].T
+        gnan = np.isnan(g).any(axis=0)
+        assert (gnan == ~fluid).all(), "NaN pattern differs from the oracle's fluid mask on level %d" % L
+        num = max(num, float(np.abs(g[:, fluid] - ref[:, fluid]).max()))
+        den = max(den, float(np.abs(ref[:, fluid]).max()))
+    return num / den
+
+
+def _pair(lbm, oracle_mod, case, precision="fp64", field=None, refine=None, flag=None):
+    f = lbm.Forest(case, precision=precision, refine=refine, flag=flag)
+    o = oracle_mod.Oracle(case, refine=refine, flag=flag)
+    field = field or inputs.uniform_field(u=case.get("u_init", (0.0, 0.0, 0.0)))
+    f.init_fields(field)
+    o.init_fields(field)
+    return f, o
+
+
+def test_block_tables_match_the_oracle(lbm, oracle_mod):
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    f = lbm.Forest(case)
+    o = oracle_mod.Oracle(case)
+    assert f.nlev == o.nlev == 4
+    for L in range(4):
+        assert (f.block_table(L) == o.leaves(L)).all()
+    assert f.cell_updates_per_coarse_step() == o.cell_updates_per_coarse_step()
+
+
+def test_cavity_fp64_matches_the_oracle_after_100_coarse_steps(lbm, oracle_mod):
+    """Two-level lid-driven cavity (32^3 coarse, centre refined), TRT, 100 coarse steps."""
+    f, o = _pair(lbm, oracle_mod, inputs.cavity_case())
+    f.step_coarse(100)
+    o.step(100)
+    assert _compare(f, o) < TOL64
+
+
+def test_uniform_periodic_fp64_matches_the_oracle(lbm, oracle_mod):
+    """Uniform periodic 64^3, SRT omega = 1.9, Taylor-Green modes + density noise, 200 steps."""
+    case = inputs.periodic_case(n=64, B=16, collision="srt", omega=1.9)
+    f, o = _pair(lbm, oracle_mod, case, field=inputs.taylor_green_field(64))
+    f.step_coarse(200)
+    o.step(200)
+    assert _compare(f, o) < TOL64
+
+
+@pytest.mark.parametrize("B", [8, 16])
+def test_three_level_periodic_fp64_matches_the_oracle(lbm, oracle_mod, B):
+    """Three levels from a ball region; interface faces, edges and corners; block size 8 and 16
+    on the same geometry (the oracle is block-free, so both must match it)."""
+    case = inputs.periodic_case(n=64, B=B, collision="trt", omega=1.7,
+                                regions=[("box", 1, (16, 16, 0), (48, 48, 64)), ("box", 2, (24, 24, 16), (40, 40, 48))],
+                                lmax=2)
+    f, o = _pair(lbm, oracle_mod, case, field=inputs.taylor_green_field(64))
+    assert f.nlev == 3
+    f.step_coarse(12)
+    o.step(12)
+    assert _compare(f, o) < TOL64
+
+
+def test_sphere_channel_fp64_matches_the_oracle(lbm, oracle_mod):
+    """The sphere-channel workload at H = 32 with B = 8: four levels, velocity inlet/outlet,
+    periodic sides, a no-slip sphere on the finest level, uniform plug start."""
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    f, o = _pair(lbm, oracle_mod, case)
+    assert f.nlev == 4
+    f.step_coarse(6)
+    o.step(6)
+    assert _compare(f, o) < TOL64
+
+
+def test_obstacle_across_an_interface_and_forced_flow(lbm, oracle_mod):
+    """A sphere that straddles a level interface (ghost cells take the coarse flag), no-slip
+    walls, body force, refinement touching a wall."""
+    case = dict(root=(4, 2, 2), B=8, lmax=1, collision="trt", rho0=1.0,
+                bc=["periodic", "periodic", "noslip", "noslip", "noslip", "noslip"],
+                bc_u=[(0, 0, 0)] * 6, spheres=[(16.0, 8.0, 8.0, 5.0)],
+                regions=[("box", 1, (0, 0, 0), (15, 16, 16))], lambda_e0=1.3, magic=3 / 16,
+                accel=(2e-5, 0.0, 0.0))
+    f, o = _pair(lbm, oracle_mod, case)
+    f.step_coarse(30)
+    o.step(30)
+    assert _compare(f, o) < TOL64
+
+
+def test_macroscopic_fields_match_the_oracle(lbm, oracle_mod):
+    case = dict(inputs.plane_poiseuille_case(B=8, ny_roots=2, where="bottom"))
+    f, o = _pair(lbm, oracle_mod, case)
+    f.step_coarse(40)
+    o.step(40)
+    for L in range(f.nlev):
+        rho, u = f.get_macroscopic(L)
+        X, Y, Z = f.cell_coords(L)
+        idx = o.lookup(L, X, Y, Z)
+        orho, ou = o.macro(L)
+        assert np.abs(rho - orho[idx]).max() < 1e-13
+        for k in range(3):
+            assert np.abs(u[k] - ou[k][idx]).max() < 1e-15
+
+
+def test_mass_and_momentum_totals(lbm, oracle_mod):
+    case = inputs.periodic_case(n=32, B=8, collision="trt", omega=1.6,
+                                regions=[("box", 1, (8, 8, 8), (24, 24, 24))], lmax=1)
+    f, o = _pair(lbm, oracle_mod, case, field=inputs.taylor_green_field(32))
+    m0 = f.reduce_mass_momentum()
+    assert np.abs(m0 - o.mass_momentum()).max() < 1e-11
+    f.step_coarse(50)
+    m1 = f.reduce_mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-13
+    assert np.abs(m1[1:] - m0[1:]).max() < 1e-12 * m0[0]
+
+
+def test_stepping_one_at_a_time_equals_stepping_in_one_call(lbm):
+    case = inputs.cavity_case()
+    a = lbm.Forest(case)
+    b = lbm.Forest(case)
+    a.init_uniform()
+    b.init_uniform()
+    for _ in range(7):
+        a.step_coarse(1)
+    b.step_coarse(7)
+    for L in range(2):
+        assert np.array_equal(a.get_pdfs(L), b.get_pdfs(L), equal_nan=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32s", "fp16s"])
+def test_checkpoint_resume_is_bit_exact(lbm, precision):
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    a = lbm.Forest(case, precision=precision)
+    a.init_uniform(case["u_init"])
+    a.step_coarse(3)
+    saved = [a.get_pdfs(L) for L in range(a.nlev)]
+    b = lbm.Forest(case, precision=precision)
+    for L in range(b.nlev):
+        b.set_pdfs(L, saved[L])
+    a.step_coarse(4)
+    b.step_coarse(4)
+    for L in range(a.nlev):
+        assert np.array_equal(a.get_pdfs(L), b.get_pdfs(L), equal_nan=True)
+
+
+def test_reduced_precision_errors_against_the_fp64_oracle(lbm, oracle_mod):
+    """Shifted FP32 and FP16 storage with FP32 collide on the two-level cavity: the velocity error
+    relative to the lid speed, against the FP64 oracle after 100 coarse steps."""
+    case = inputs.cavity_case()
+    o = oracle_mod.Oracle(case)
+    o.init_fields(inputs.uniform_field())
+    o.step(100)
+    errs = {}
+    for prec in ("fp32s", "fp16s"):
+        f = lbm.Forest(case, precision=prec)
+        f.init_uniform()
+        f.step_coarse(100)
+        e = 0.0
+        for L in range(2):
+            rho, u = f.get_macroscopic(L)
+            X, Y, Z = f.cell_coords(L)
+            idx = o.lookup(L, X, Y, Z)
+            orho, ou = o.macro(L)
+            e = max(e, max(float(np.abs(u[k] - ou[k][idx]).max()) for k in range(3)) / 0.05)
+        errs[prec] = e
+    assert errs["fp32s"] < 1e-5
+    assert errs["fp16s"] < 2e-3
+
+
+def test_timing_api_reports_every_launch(lbm):
+    case = inputs.cavity_case()
+    f = lbm.Forest(case)
+    f.init_uniform()
+    f.step_coarse(2)
+    f.timing_begin(5)
+    f.step_coarse(5)
+    ms, cnt = f.timing_end()
+    assert cnt.tolist() == [5, 10]
+    assert (ms > 0).all()
+    assert f.launches_per_coarse_step() == 3

@@ -1,0 +1,101 @@
+"""CPU-only checks of the C-ABI library: it loads without a GPU, exports every entry point
+declared in include/lbm_gb300.h, and its host-side forest planner agrees exactly with the
+oracle's independent forest (leaf sets and cell counts are integer results: bit-exact)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1508_07982_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1508_07982_gb300 import build, lbm as mod
+    build.build()
+    return mod
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lbm_gb300.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|const char\*)\s+(lbm_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    lib = lbm.library()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(lbm.EXPORTS) == declared
+
+
+def test_lattice_order_matches_the_oracle(lbm, oracle_mod):
+    e, w, opp = lbm.lbm_lattice()
+    e2, w2, opp2 = oracle_mod.lattice()
+    assert (e == e2).all() and (opp == opp2).all()
+    assert np.abs(w - w2).max() == 0.0
+
+
+def test_invalid_descriptions_are_rejected_on_the_host(lbm):
+    bad = [
+        dict(inputs.cavity_case(), B=12),
+        dict(inputs.cavity_case(), lmax=9),
+        dict(inputs.cavity_case(), bc=["periodic", "noslip", "noslip", "noslip", "noslip", "noslip"]),
+        dict(inputs.cavity_case(), rho0=0.0),
+    ]
+    for case in bad:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.Plan(case)
+        assert ei.value.status == lbm.LBM_EINVAL
+
+
+def _cases():
+    yield "cavity", inputs.cavity_case(), None
+    yield "channel", inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5)), None
+    yield "poiseuille", inputs.plane_poiseuille_case(B=8, where="both"), None
+    yield "periodic-ball", inputs.periodic_case(n=64, B=8, collision="trt", omega=1.7,
+                                                regions=[("ball", 3, (5, 60, 33), 9.0)], lmax=3), None
+    rng = np.random.default_rng(7)
+    marks = {}
+
+    def refine(L, x, y, z, user):
+        k = (L, x, y, z)
+        if k not in marks:
+            marks[k] = rng.random() < (0.3 if L == 0 else 0.12)
+        return int(marks[k])
+
+    yield "random", dict(root=(3, 2, 2), B=8, lmax=3, collision="trt", rho0=1.0,
+                         bc=["periodic", "periodic", "noslip", "noslip", "velocity", "velocity"],
+                         bc_u=[(0, 0, 0)] * 4 + [(0.01, 0, 0)] * 2, spheres=[(9.0, 7.0, 5.0, 3.3)],
+                         regions=[]), refine
+
+
+@pytest.mark.parametrize("name", ["cavity", "channel", "poiseuille", "periodic-ball", "random"])
+def test_host_planner_matches_the_oracle_forest(lbm, oracle_mod, name):
+    case, refine = next((c, r) for n, c, r in _cases() if n == name)
+    memo = {}
+
+    def cached(L, x, y, z, user):        # both sides must see the same callback answers
+        k = (L, x, y, z)
+        if k not in memo:
+            memo[k] = refine(L, x, y, z, user)
+        return memo[k]
+
+    cb = cached if refine else None
+    p = lbm.Plan(case, refine=cb)
+    o = oracle_mod.Oracle(case, refine=cb)
+    assert p.nlev == o.nlev
+    for L in range(p.nlev):
+        a = p.leaves(L)
+        b = o.leaves(L)
+        assert a.shape == b.shape and (a == b).all(), "leaf set differs on level %d" % L
+        c = p.counts(L)
+        oc = o.counts(L)
+        assert c["fluid"] == oc["fluid"]
+        # the planner's ghost work list is the oracle's stream set minus its owned fluid cells
+        assert c["ghost12"] == oc["stream"] - oc["fluid"]
