@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Refined-grid D3Q19 benchmark: GLUPS and % of the HBM roofline, FP16/FP32 vs FP64.
+
+Workload: the refined channel past a sphere (4 levels, 2:1-balanced blocks of 32^3
+cells, 8.39M cells, 28.0M cell updates per coarse step, velocity inlet/outlet,
+periodic sides, Re 100, TRT with Lambda = 3/16).  One timed step is one coarse time
+step: the whole recursive level schedule (15 fused level kernels), replayed as a CUDA
+graph, with the inputs resident in HBM.  GLUPS = sum_L (owned fluid cells of level L)
+x 2^L / time per coarse step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the method has no
+cross-replica exchange); rank 0 prints one JSON line.  `--impl reference` times the
+plain CPU oracle on the host cores (rank 0 only), one full coarse step per timed step.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "refined-grid D3Q19 GLUPS & % HBM roofline, FP16/FP32 vs FP64; ms/coarse step"
+UNIT = "GLUPS"
+BYTES_PER_VALUE = {"fp64": 8, "fp32s": 4, "fp16s": 2}
+DTYPE = {"fp64": "f64", "fp32s": "f32", "fp16s": "f32 compute / f16 storage"}
+WORKLOAD = "sphere_channel_4lvl_32cube_8.39Mcells"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32s", choices=["fp64", "fp32s", "fp16s"])
+    p.add_argument("--no-variants", action="store_true", help="skip the FP64/FP16 side measurements")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    return p.parse_args()
+
+
+def _config(case, f=None):
+    cfg = {"workload": WORKLOAD, "domain_cells_level0": [case["root"][a] * case["B"] for a in range(3)],
+           "block_cells": case["B"], "levels": case["lmax"] + 1, "collision": "trt", "magic": 3.0 / 16.0,
+           "lambda_e0": round(case["lambda_e0"], 6), "refine_radii": [r[3] for r in case["regions"]],
+           "l2": "inputs larger than L2 (PDF grids exceed the 129 MB L2 several times over)"}
+    if f is not None:
+        cfg["cell_updates_per_coarse_step"] = f.cell_updates_per_coarse_step()
+        cfg["leaf_blocks_per_level"] = [len(f.block_table(L)) for L in range(f.nlev)]
+    return cfg
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region (read-only queries)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "kernels_impl.cuh", "kernels_f32.cu", "kernels_f64.cu", "kernels_f16.cu", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1508_07982_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(precision):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the kernel source that is built now; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(precision)
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _run_timed(lbm, torch, case, precision, steps, warmup, timing=True):
+    f = lbm.Forest(case, precision=precision)
+    f.init_uniform(case["u_init"])
+    f.step_coarse(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    if timing:
+        f.timing_begin(steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.step_coarse(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lev = f.timing_end() if timing else None
+    return f, ms, lev
+
+
+def _roofline(f, lev, precision, peaks, peak_kind):
+    ms_l, cnt_l = lev
+    share = ms_l / ms_l.sum()
+    L = int(np.argmax(ms_l))
+    counts = _fluid_counts(f)
+    bytes_per_launch = counts[L] * 2 * 19 * BYTES_PER_VALUE[precision]
+    avg_s = ms_l[L] / cnt_l[L] / 1e3
+    achieved = bytes_per_launch / avg_s / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = _ncu_traffic(precision)
+    per_level = [{"level": i, "launches": int(cnt_l[i]), "ms_total": round(float(ms_l[i]), 4),
+                  "share": round(float(share[i]), 4),
+                  "GBps_algorithmic": round(counts[i] * 2 * 19 * BYTES_PER_VALUE[precision] / (ms_l[i] / cnt_l[i] / 1e3) / 1e9, 1)
+                  if cnt_l[i] else None} for i in range(f.nlev)]
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": "step_kernel level %d (finest) fused stream-collide" % L,
+            "bytes_per_launch_algorithmic": int(bytes_per_launch),
+            "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "per_level": per_level}
+
+
+_COUNTS = {}
+
+
+def _fluid_counts(f):
+    key = repr(sorted(f.case.items()))
+    if key not in _COUNTS:
+        from paper_1508_07982_gb300 import lbm
+        p = lbm.Plan(f.case)
+        _COUNTS[key] = [p.counts(L)["fluid"] for L in range(p.nlev)]
+    return _COUNTS[key]
+
+
+def _e2e(lbm, torch, case, precision, steps):
+    """Same metric through the public API with host buffers: init from pinned host (rho, u) of every
+    level, `steps` coarse steps each followed by the FP64 mass/momentum totals read back to the
+    host, then the macroscopic fields of every level read back."""
+    f = lbm.Forest(case, precision=precision)
+    host_in = []
+    for L in range(f.nlev):
+        n = f.n_cells(L)
+        rho = torch.ones(n, dtype=torch.float64).pin_memory()
+        u = torch.zeros(3, n, dtype=torch.float64).pin_memory()
+        u[0] = case["u_init"][0]
+        host_in.append((rho, u))
+    host_out = [(torch.empty(f.n_cells(L), dtype=torch.float64).pin_memory(),
+                 torch.empty(3, f.n_cells(L), dtype=torch.float64).pin_memory()) for L in range(f.nlev)]
+    h2d = sum(r.numel() * 8 + u.numel() * 8 for r, u in host_in)
+    d2h_end = sum(r.numel() * 8 + u.numel() * 8 for r, u in host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for L, (rho, u) in enumerate(host_in):
+        f.init_equilibrium(L, rho, u, on_device=False)
+    for _ in range(steps):
+        f.step_coarse(1)
+        f.reduce_mass_momentum()
+    for L, (rho, u) in enumerate(host_out):
+        f.get_macroscopic(L, rho, u, on_device=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    upd = f.cell_updates_per_coarse_step() * steps
+    f.close()
+    return {"value": round(upd / dt / 1e9, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d // steps),
+            "d2h_bytes_per_step": int((d2h_end + 32 * steps) // steps),
+            "note": "lbm_init_equilibrium from pinned host (rho,u) of all levels, %d x (lbm_step_coarse(1) + "
+                    "lbm_reduce_mass_momentum to host), lbm_get_macroscopic of all levels to pinned host" % steps}
+
+
+def _precision_error(fa, fb):
+    """Velocity and density error of forest fa against forest fb (FP64) over owned fluid cells."""
+    du, dr, umax = 0.0, 0.0, 0.0
+    for L in range(fa.nlev):
+        ra, ua = fa.get_macroscopic(L)
+        rb, ub = fb.get_macroscopic(L)
+        ok = np.isfinite(rb)
+        du = max(du, float(np.abs(ua[:, ok] - ub[:, ok]).max()))
+        dr = max(dr, float(np.abs(ra[ok] - rb[ok]).max()))
+        umax = max(umax, float(np.abs(ub[:, ok]).max()))
+    return {"u_linf_rel_to_umax": du / umax, "rho_linf": dr}
+
+
+def _cpu_baseline(case, steps=2):
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    o = oracle.Oracle(case)
+    o.init_fields(_uniform(case))
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    upd = o.cell_updates_per_coarse_step() * steps
+    return {"value": round(upd / dt / 1e9, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d full coarse steps of the same 8.39M-cell forest in FP64 (%.1f s; setup %.1f s excluded)"
+                      % (steps, dt, setup)}
+
+
+def _uniform(case):
+    from paper_1508_07982_gb300 import inputs
+    return inputs.uniform_field(u=case["u_init"])
+
+
+def run_reference(args, case):
+    """The plain CPU oracle as the reference arm: each timed step is one full coarse step."""
+    from oracle import oracle
+    oracle.build()
+    o = oracle.Oracle(case)
+    o.init_fields(_uniform(case))
+    o.step(min(args.warmup, 1))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    upd = o.cell_updates_per_coarse_step() * args.steps
+    v = upd / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(case),
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d full coarse steps of the workload in FP64 on the host cores" % args.steps},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    from paper_1508_07982_gb300 import inputs
+    case = inputs.sphere_channel_case()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, case)
+        return
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1508_07982_gb300 import build, lbm
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    build.build()
+    peaks, peak_kind = _measured_peaks()
+
+    # ---- timed region: K coarse steps of the resident workload, graph replay, events per kernel
+    f = lbm.Forest(case, precision=args.precision)
+    f.init_uniform(case["u_init"])
+    f.step_coarse(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    launches = f.launches_per_coarse_step()
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    f.timing_begin(args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.step_coarse(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    lev = f.timing_end()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = f.cell_updates_per_coarse_step()
+    value = world * upd * args.steps / (ms / 1e3) / 1e9
+    roof = _roofline(f, lev, args.precision, peaks, peak_kind)
+    cfg = _config(case, f)
+    mass = f.reduce_mass_momentum()
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        ref64 = None
+        for prec in ("fp64", "fp32s", "fp16s"):
+            k = max(args.steps // 4, 20)
+            g, ms_v, lev_v = _run_timed(lbm, torch, case, prec, k, 3)
+            entry = {"value": round(upd * k / (ms_v / 1e3) / 1e9, 3), "unit": UNIT,
+                     "ms_per_step": round(ms_v / k, 4), "steps": k}
+            r = _roofline(g, lev_v, prec, peaks, peak_kind)
+            entry["roofline"] = {kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+            if prec == "fp64":
+                ref64 = g
+            else:
+                entry["error_vs_fp64_after_%d_steps" % (k + 3)] = _precision_error(g, ref64)
+                g.close()
+            variants[prec] = entry
+        if ref64 is not None:
+            ref64.close()
+
+    e2e = _e2e(lbm, torch, case, args.precision, min(args.steps, 200)) if rank == 0 and not args.no_e2e else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = _cpu_baseline(case)
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": dict(cfg, precision=args.precision, parallelism="replicas" if world > 1 else "single"),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches * args.steps), "mass_total": mass[0]}
+    if variants:
+        line["precisions"] = variants
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    f.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -40,6 +40,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 #define ORC_MAXLEV 8
@@ -826,3 +829,12 @@ long orc_num_fluid(const orc *o, int L) { return o->lv[L].nC; }
 long orc_num_stream(const orc *o, int L) { return o->lv[L].nS; }
 long orc_num_ghost(const orc *o, int L) { return o->lv[L].nG; }
 long orc_num_coalesce(const orc *o, int L) { return o->lv[L].nK; }
+
+/* Threads the OpenMP loops use (1 without OpenMP). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -89,6 +89,7 @@ def lib():
             getattr(L, nm).restype = ctypes.c_long
             getattr(L, nm).argtypes = [P, ctypes.c_int]
         L.orc_lattice.argtypes = [ip, dp, ip]
+        L.orc_num_threads.restype = ctypes.c_int
         L.orc_feq.argtypes = [ctypes.c_double, dp, ctypes.c_double, dp]
         L.orc_collide.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_double]
         L.orc_scale_rate.restype = ctypes.c_double
@@ -105,6 +106,10 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def num_threads():
+    return lib().orc_num_threads()
 
 
 def lattice():

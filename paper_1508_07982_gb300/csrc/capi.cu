@@ -189,12 +189,12 @@ lbm_status capture(lbm_forest* f, int timed, int parity) {
     CU(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal));
     for (size_t k = 0; k < f->sched.size(); k++) {
         const Launch& l = f->sched[k];
-        if (timed) cudaEventRecord(evs[k], f->cap);
+        if (timed) CU(cudaEventRecordWithFlags(evs[k], f->cap, cudaEventRecordExternal));
         StepArgs a = make_args(f, l, cur);
         f->L->step(a, f->plan.d.collision, l.grid, f->cap);
         cur[l.level] ^= 1;
     }
-    if (timed) cudaEventRecord(evs.back(), f->cap);
+    if (timed) CU(cudaEventRecordWithFlags(evs.back(), f->cap, cudaEventRecordExternal));
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(f->cap, &g);
     if (le != cudaSuccess) {

@@ -56,7 +56,7 @@ def periodic_case(n=64, B=16, collision="srt", omega=1.9, regions=(), lmax=0):
                 accel=(0.0, 0.0, 0.0))
 
 
-SPHERE_CHANNEL_RADII = (40.0, 24.0, 13.0)
+SPHERE_CHANNEL_RADII = (34.0, 12.0, 6.0)
 
 
 def sphere_channel_case(H=64, B=32, radii=SPHERE_CHANNEL_RADII, u_in=0.04, Re=100.0):

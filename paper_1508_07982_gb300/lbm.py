@@ -123,6 +123,14 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _host_f64(x):
+    """Passes numpy FP64 arrays and torch tensors through; converts anything else to FP64."""
+    if x is None or hasattr(x, "data_ptr") or (isinstance(x, np.ndarray) and x.dtype == np.float64
+                                               and x.flags.c_contiguous):
+        return x
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
 def lbm_lattice():
     e = np.zeros((Q, 3), np.int32)
     w = np.zeros(Q)
@@ -278,14 +286,9 @@ class Forest:
         _check(library().lbm_set_level_params_explicit(self.h, _dp(le), _dp(lo), _dp(acc)))
 
     def init_equilibrium(self, level, rho=None, u=None, on_device=False):
-        keep = []
-        if not on_device:
-            if rho is not None:
-                rho = np.ascontiguousarray(rho, dtype=np.float64)
-                keep.append(rho)
-            if u is not None:
-                u = np.ascontiguousarray(u, dtype=np.float64)
-                keep.append(u)
+        """rho [n_cells] and u [3][n_cells], FP64, block-major; numpy arrays, or torch tensors
+        (host tensors may be pinned; device tensors need on_device=True)."""
+        rho, u = _host_f64(rho), _host_f64(u)
         _check(library().lbm_init_equilibrium(self.h, level, _ptr(rho), _ptr(u), 1 if on_device else 0))
 
     def init_uniform(self, u=(0.0, 0.0, 0.0)):
@@ -308,13 +311,11 @@ class Forest:
         _check(library().lbm_step_coarse(self.h, n))
 
     def get_macroscopic(self, level, rho=None, u=None, on_device=False):
-        if on_device:
-            _check(library().lbm_get_macroscopic(self.h, level, _ptr(rho), _ptr(u), 1))
-            return rho, u
-        n = self.n_cells(level)
-        rho = np.zeros(n)
-        u = np.zeros((3, n))
-        _check(library().lbm_get_macroscopic(self.h, level, rho.ctypes.data, u.ctypes.data, 0))
+        """Returns (rho, u); allocates numpy outputs when none are given and on_device is False."""
+        if rho is None and u is None and not on_device:
+            n = self.n_cells(level)
+            rho, u = np.zeros(n), np.zeros((3, n))
+        _check(library().lbm_get_macroscopic(self.h, level, _ptr(rho), _ptr(u), 1 if on_device else 0))
         return rho, u
 
     def get_pdfs(self, level, out=None, on_device=False):
@@ -328,8 +329,7 @@ class Forest:
         return out
 
     def set_pdfs(self, level, pdfs, on_device=False):
-        if not on_device:
-            pdfs = np.ascontiguousarray(pdfs, dtype=np.float64)
+        pdfs = _host_f64(pdfs)
         _check(library().lbm_set_pdfs(self.h, level, _ptr(pdfs), 1 if on_device else 0))
 
     def reduce_mass_momentum(self):
