@@ -54,6 +54,7 @@ struct DevBuf {
     uint8_t* cell = nullptr;
     int32_t *nbr = nullptr, *parent = nullptr, *child = nullptr, *pos = nullptr, *gcells = nullptr;
     uint8_t* kind = nullptr;
+    uint32_t* link = nullptr;
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -111,6 +112,8 @@ struct lbm_forest {
     int tmax = 0, tused = 0;
     std::vector<cudaEvent_t> tev;
     int64_t updates = 0;
+    int lzc = 3;        // log2 of the cells per thread along z in the owned part of the step kernel
+    int minb = 3;       // CTAs per SM of the step-kernel variant
 };
 
 namespace {
@@ -147,19 +150,23 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.cur_f = L + 1 < n ? cur[L + 1] : 0;
     a.substep = l.substep;
     a.LB = f->plan.LB;
+    a.lzc = f->lzc;
+    a.minb = f->minb;
     a.per = (f->plan.per[0] ? 1 : 0) | (f->plan.per[1] ? 2 : 0) | (f->plan.per[2] ? 4 : 0);
     a.params = f->d_params + L;
     a.wall = f->d_wall;
     a.rho0 = f->plan.d.rho0;
+    a.inv_rho0 = 1.0 / f->plan.d.rho0;
     return a;
 }
 
 void build_schedule(lbm_forest* f) {
     f->sched.clear();
-    const int n = f->plan.nlev, B3 = f->plan.B * f->plan.B * f->plan.B;
+    const int n = f->plan.nlev, B = f->plan.B;
     auto push = [&](int L, int s) {
         const HostLevel& V = f->plan.lv[L];
-        int grid = V.nown * (B3 / 256) + int((V.gcells.size() + 255) / 256);
+        const int64_t units = int64_t(V.nown) * B * B * (B >> f->lzc);
+        int grid = int((units + 255) / 256) + int((V.gcells.size() + 255) / 256);
         f->sched.push_back({L, s, grid});
     };
     std::function<void(int)> rec = [&](int L) {
@@ -333,6 +340,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.pos);
         cudaFree(b.gcells);
         cudaFree(b.kind);
+        cudaFree(b.link);
     }
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
@@ -382,7 +390,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         lbm_status s;
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
-            (s = upload(&b.kind, V.kind)))
+            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)))
             return bail(s);
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -394,6 +402,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.pos = b.pos;
         g.kind = b.kind;
         g.gcells = b.gcells;
+        g.link = b.link;
         g.nown = V.nown;
         g.nbricks = V.nbricks();
         g.ngcells = int(V.gcells.size());
@@ -424,6 +433,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
         cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
         return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
+    // cells per thread along z: 8 for 32^3 blocks, 4 for 16^3, 2 for 8^3
+    f->lzc = P.LB - 2;
     build_schedule(f);
     *out = f;
     return LBM_OK;
@@ -469,8 +480,10 @@ lbm_status lbm_set_level_params_explicit(lbm_forest* f, const double* le, const 
         h.le = le[L];
         h.lo = P.d.collision == LBM_TRT ? lo[L] : le[L];
         for (int k = 0; k < 3; k++) h.acc[k] = acc ? acc[3 * L + k] : 0.0;
-        for (int q = 0; q < Q; q++)
-            h.force[q] = 3.0 * weight(q) * P.d.rho0 * (EX[q] * h.acc[0] + EY[q] * h.acc[1] + EZ[q] * h.acc[2]);
+        for (int k = 0; k < 3; k++) h.fa[k] = 3.0 * P.d.rho0 * h.acc[k];
+        h.lef = float(h.le);
+        h.lof = float(h.lo);
+        for (int k = 0; k < 3; k++) h.faf[k] = float(h.fa[k]);
     }
     CU(cudaMemcpyAsync(f->d_params, f->hp.data(), sizeof(LevelParams) * P.nlev, cudaMemcpyHostToDevice, f->stream));
     CU(cudaStreamSynchronize(f->stream));
@@ -627,6 +640,26 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
     for (int k = 0; k < 4; k++) out[k] = f->h_out[k];
     for (int k = 0; k < 4; k++)
         if (!std::isfinite(out[k])) return fail(LBM_ENONFINITE, "non-finite total (component %d)", k);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_kernel_config(lbm_forest* f, int32_t cells_per_thread_log2, int32_t ctas_per_sm) {
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    if (cells_per_thread_log2 < 0 || cells_per_thread_log2 > f->plan.LB)
+        return fail(LBM_EINVAL, "cells per thread must be 2^k with 2^k <= B");
+    if (ctas_per_sm != 2 && ctas_per_sm != 3) return fail(LBM_EINVAL, "ctas_per_sm must be 2 or 3");
+    CU(cudaStreamSynchronize(f->stream));
+    free_graphs(f);
+    f->lzc = cells_per_thread_log2;
+    f->minb = ctas_per_sm;
+    build_schedule(f);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm) {
+    if (!f || !cells_per_thread_log2 || !ctas_per_sm) return fail(LBM_EINVAL, "NULL argument");
+    *cells_per_thread_log2 = f->lzc;
+    *ctas_per_sm = f->minb;
     return LBM_OK;
 }
 

@@ -269,6 +269,41 @@ struct Builder {
         return true;
     }
 
+    // Per owned cell: which of the 18 pulls need the general path (source not an owned fluid
+    // cell of this level, or a PDF that coalescence replaces), and whether the cell is fluid.
+    void links(int L) {
+        HostLevel& V = p.lv[L];
+        const int B = p.B, B3 = B * B * B, M = B - 1;
+        V.link.assign(size_t(V.nown) * B3, 0u);
+        for (int k = 0; k < V.nown; k++) {
+            const int32_t* nbr = &V.nbr[size_t(k) * 27];
+            const bool finer = V.kind[k] & BK_TOUCH_FINER;
+            for (int z = 0; z < B; z++)
+                for (int y = 0; y < B; y++)
+                    for (int x = 0; x < B; x++) {
+                        const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
+                        uint32_t m = 0;
+                        if (V.cell[c] != CK_FLUID) m |= 1u << 31;
+                        for (int q = 1; q < Q; q++) {
+                            int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
+                            for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
+                            int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
+                            bool plain = nb >= 0 && nb < V.nown &&
+                                         V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] == CK_FLUID;
+                            if (plain && finer) {
+                                bool coal = nb == NB_FINER;
+                                if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
+                                if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
+                                if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
+                                plain = !coal;
+                            }
+                            if (!plain) m |= 1u << q;
+                        }
+                        V.link[c] = m;
+                    }
+        }
+    }
+
     void children(int L) {
         HostLevel& V = p.lv[L];
         V.child.assign(size_t(V.nown) * 8, -1);
@@ -348,6 +383,13 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
     for (int L = 0; L < p.nlev; L++)
         if (!b.bricks(L, err)) return false;
     for (int L = 0; L < p.nlev; L++) b.children(L);
+    for (int L = 0; L < p.nlev; L++) {
+        if (int64_t(p.lv[L].nbricks()) * p.B * p.B * p.B >= (int64_t(1) << 31)) {
+            err = "a level holds more than 2^31 cells";
+            return false;
+        }
+        b.links(L);
+    }
     return true;
 }
 

@@ -12,8 +12,10 @@ namespace lbm {
 // Per-level parameters, device-resident so that captured graphs never need rebuilding.
 struct LevelParams {
     double le, lo;        // lambda_e, lambda_o (omega, omega for SRT)
-    double force[19];     // 3 w_a rho0 (e_a . a_L)
+    double fa[3];         // 3 rho0 a_L: the body force term is F_a = w_a (e_a . fa), Sec. 2.1
     double acc[3];        // a_L
+    float lef, lof;       // the same in FP32, for the FP32-arithmetic kernels
+    float faf[3];
 };
 
 struct DevLevel {
@@ -25,6 +27,8 @@ struct DevLevel {
     const int32_t* pos;   // [nbricks][3]
     const uint8_t* kind;  // [nbricks]
     const int32_t* gcells;
+    const uint32_t* link; // [nown * B^3] per owned cell: bit q set = link q needs the general pull;
+                          // bit 31 = the cell is not a fluid cell
     int nown, nbricks, ngcells;
     int64_t ncells;
     int N[3];
@@ -35,11 +39,17 @@ struct StepArgs {
     int cur, cur_c, cur_f;
     int substep;          // 1: ghost layers hold exploded values; 2: they hold sub-step-1 values
     int LB;
+    int lzc;              // log2 of the cells each thread walks along z
+    int minb;             // CTAs per SM the kernel variant is compiled for (2 or 3)
     int per;              // bit a set: axis a periodic
     const LevelParams* params;
     const double* wall;   // [6][19] 6 w_a rho0 (e_a . u_w) per face
-    double rho0;
+    double rho0, inv_rho0;
 };
+
+// Bits of the per-cell link mask.
+constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
+constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18
 
 // Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).
 struct Launchers {

@@ -6,10 +6,21 @@ namespace lbm {
 
 template <typename T, typename C>
 struct LaunchImpl {
+    template <int COLL, int MINB>
+    static void step_m(const StepArgs& a, int grid, cudaStream_t s) {
+        if (a.LB == 3) step_kernel<T, C, COLL, 3, MINB><<<grid, 256, 0, s>>>(a);
+        else if (a.LB == 4) step_kernel<T, C, COLL, 4, MINB><<<grid, 256, 0, s>>>(a);
+        else step_kernel<T, C, COLL, 5, MINB><<<grid, 256, 0, s>>>(a);
+    }
+    template <int COLL>
+    static void step_b(const StepArgs& a, int grid, cudaStream_t s) {
+        if (a.minb == 2) step_m<COLL, 2>(a, grid, s);
+        else step_m<COLL, 3>(a, grid, s);
+    }
     static void step(const StepArgs& a, int collision, int grid, cudaStream_t s) {
         if (grid <= 0) return;
-        if (collision == LBM_TRT) step_kernel<T, C, LBM_TRT><<<grid, 256, 0, s>>>(a);
-        else step_kernel<T, C, LBM_SRT><<<grid, 256, 0, s>>>(a);
+        if (collision == LBM_TRT) step_b<LBM_TRT>(a, grid, s);
+        else step_b<LBM_SRT>(a, grid, s);
     }
     static void init(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, const double* rho,
                      const double* u, int uniform, const double uc[4], int collision, cudaStream_t s) {

@@ -39,6 +39,8 @@ struct HostLevel {
     std::vector<uint8_t> kind;     // [nbricks] BK_* bits
     std::vector<uint8_t> cell;     // [nbricks * B^3] CK_* per cell
     std::vector<int32_t> gcells;   // cell indices of CK_GHOST cells (the ghost work list)
+    std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
+                                   // same-level load; bit 31 = not a fluid cell
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }
 };

@@ -59,8 +59,9 @@ template <> __device__ __forceinline__ float qnan<float>() { return __int_as_flo
 // SRT: f~ = f - omega (f - f^eq) + F;  TRT: f~ = f - le (f+ - f^eq+) - lo (f- - f^eq-) + F, with
 // f^eq of Eq. (fequ) and F_a = 3 w_a rho0 e_a . a (Sec. 2.1); the velocity inside f^eq is
 // sum_a e_a f_a / rho0, unmodified by the force.
+// The body force enters as fa = 3 rho0 a (three values): F_q = w_q (e_q . fa), F_opp(q) = -F_q.
 template <typename C, int COLL>
-__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&F)[19], C rho0, C inv_rho0) {
+__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0) {
     C R = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
     for (int q = 0; q < 19; q++) {
@@ -83,7 +84,12 @@ __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&F)[19]
         if (dex(q)) eu += dex(q) > 0 ? ux : -ux;
         if (dey(q)) eu += dey(q) > 0 ? uy : -uy;
         if (dez(q)) eu += dez(q) > 0 ? uz : -uz;
+        C ea = C(0);
+        if (dex(q)) ea += dex(q) > 0 ? fa[0] : -fa[0];
+        if (dey(q)) ea += dey(q) > 0 ? fa[1] : -fa[1];
+        if (dez(q)) ea += dez(q) > 0 ? fa[2] : -fa[2];
         const C w = C(dw(q));
+        const C Fq = w * ea;
         const C eqp = w * (R + rho0 * (C(4.5) * eu * eu) - base);
         const C eqm = w * rho0 * C(3.0) * eu;
         if (COLL == LBM_TRT) {
@@ -91,13 +97,13 @@ __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&F)[19]
             const C fm = C(0.5) * (v[q] - v[p]);
             const C dp = le * (fp - eqp);
             const C dm = lo * (fm - eqm);
-            const C a = v[q] - dp - dm + F[q];
-            const C b = v[p] - dp + dm + F[p];
+            const C a = v[q] - dp - dm + Fq;
+            const C b = v[p] - dp + dm - Fq;
             v[q] = a;
             v[p] = b;
         } else {
-            const C a = v[q] - le * (v[q] - (eqp + eqm)) + F[q];
-            const C b = v[p] - le * (v[p] - (eqp - eqm)) + F[p];
+            const C a = v[q] - le * (v[q] - (eqp + eqm)) + Fq;
+            const C b = v[p] - le * (v[p] - (eqp - eqm)) - Fq;
             v[q] = a;
             v[p] = b;
         }
@@ -145,108 +151,160 @@ struct Access {
     }
 };
 
-// One sub-step of one level: stream (pull) + boundary + explosion reads + coalescence, then
-// collide owned cells (Alg. 2 StreamCollide generalised to every level).  CTAs [0, nown * B^3/256)
-// cover owned bricks; the rest cover the ghost-layer-1/2 work list.
-template <typename T, typename C, int COLL>
-__global__ void __launch_bounds__(256) step_kernel(const StepArgs a) {
-    const int LB = a.LB, B = 1 << LB, M = B - 1, B3s = 3 * LB;
-    const int cpb = (1 << B3s) >> 8;
-    const int owned_ctas = a.lv.nown * cpb;
-    int brick, local;
-    bool ghost;
-    if (int(blockIdx.x) < owned_ctas) {
-        brick = blockIdx.x / cpb;
-        local = (blockIdx.x - brick * cpb) * 256 + threadIdx.x;
-        ghost = false;
-    } else {
-        const int i = (blockIdx.x - owned_ctas) * 256 + threadIdx.x;
-        if (i >= a.lv.ngcells) return;
-        const int c = __ldg(a.lv.gcells + i);
-        brick = c >> B3s;
-        local = c & ((1 << B3s) - 1);
-        ghost = true;
-    }
-    const int64_t cidx = (int64_t(brick) << B3s) + local;
-    const uint8_t bk = __ldg(a.lv.kind + brick);
-    if (!ghost && !(bk & BK_PURE) && __ldg(a.lv.cell + cidx) != CK_FLUID) return;
-    const int lx = local & M, ly = (local >> LB) & M, lz = local >> (2 * LB);
+// Compute-precision view of the per-level parameters.
+template <typename C> struct Par;
+template <> struct Par<double> {
+    __device__ __forceinline__ static double le(const LevelParams* P) { return P->le; }
+    __device__ __forceinline__ static double lo(const LevelParams* P) { return P->lo; }
+    __device__ __forceinline__ static double fa(const LevelParams* P, int k) { return P->fa[k]; }
+};
+template <> struct Par<float> {
+    __device__ __forceinline__ static float le(const LevelParams* P) { return P->lef; }
+    __device__ __forceinline__ static float lo(const LevelParams* P) { return P->lof; }
+    __device__ __forceinline__ static float fa(const LevelParams* P, int k) { return P->faf[k]; }
+};
+
+// General pull of direction q into cell (x, y, z) of brick `brick` (owned or ghost): neighbour
+// lookup through the 27-entry table, then by the class of the source cell
+//   - coalescence (owned x only): mean of the 8 finer children of x (Eq. ftoc);
+//   - obstacle or domain wall: bounce-back of the own opposite value (Sec. 2.2), plus the
+//     velocity term on velocity walls; a cell beyond several faces takes the first of
+//     z+, z-, y+, y-, x+, x-;
+//   - owned fluid, or ghost layer 1-2 in the second sub-step: the stored value;
+//   - ghost layer 1-2 in the first sub-step, or ghost layer 3+: the coarse parent (Eq. ctof).
+// In the first sub-step a ghost cell's own value is its coarse parent as well.
+template <typename T, typename C, int LB>
+__device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick, int x, int y, int z, int q,
+                          bool ghost) {
+    constexpr int B = 1 << LB, M = B - 1, B3s = 3 * LB;
+    const int ex = dex(q), ey = dey(q), ez = dez(q);
+    const int sx = x - ex, sy = y - ey, sz = z - ez;
+    const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+    const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+    const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
+    const int* nbr = a.lv.nbr + brick * 27;
+    const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
     const void* src = a.lv.f[a.cur];
     const int64_t n = a.lv.ncells;
-    const Access<T, C> acc{a, LB, M};
-    // in the first sub-step the ghost layers hold the exploded coarse values (Eq. ctof)
+    const int64_t cidx = (int64_t(brick) << B3s) + (z << (2 * LB)) + (y << LB) + x;
     const bool exploded_self = ghost && a.substep == 1;
-    const bool touch_finer = !ghost && (bk & BK_TOUCH_FINER);
-    const int* nbr = a.lv.nbr + brick * 27;
+    if (!ghost && (__ldg(a.lv.kind + brick) & BK_TOUCH_FINER)) {
+        bool coal = nb == NB_FINER;
+        if (!coal && ex && ox) coal = __ldg(nbr + 13 + ox) == NB_FINER;
+        if (!coal && ey && oy) coal = __ldg(nbr + 13 + 3 * oy) == NB_FINER;
+        if (!coal && ez && oz) coal = __ldg(nbr + 13 + 9 * oz) == NB_FINER;
+        if (coal) return acc.children_mean(brick, x, y, z, q);
+    }
+    const int qo = dopp(q);
+    if (nb >= 0) {
+        const int tx = sx & M, ty = sy & M, tz = sz & M;
+        const int64_t sidx = (int64_t(nb) << B3s) + (tz << (2 * LB)) + (ty << LB) + tx;
+        const uint8_t ck = (__ldg(a.lv.kind + nb) & BK_PURE) ? uint8_t(CK_FLUID) : __ldg(a.lv.cell + sidx);
+        if (ck == CK_SOLID)
+            return exploded_self ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
+        if (ck == CK_FLUID || (ck == CK_GHOST && a.substep == 2)) return acc.load(src, n, q, sidx);
+        return acc.coarse(nb, tx, ty, tz, q);
+    }
+    if (nb == NB_WALL) {
+        const int* P = a.lv.pos + 3 * brick;
+        const int gx = P[0] * B + sx, gy = P[1] * B + sy, gz = P[2] * B + sz;
+        int face;
+        if (!(a.per & 4) && gz >= a.lv.N[2]) face = 5;
+        else if (!(a.per & 4) && gz < 0) face = 4;
+        else if (!(a.per & 2) && gy >= a.lv.N[1]) face = 3;
+        else if (!(a.per & 2) && gy < 0) face = 2;
+        else if (!(a.per & 1) && gx >= a.lv.N[0]) face = 1;
+        else face = 0;
+        const C own = exploded_self ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
+        return own + C(__ldg(a.wall + face * 19 + q));
+    }
+    return qnan<C>();
+}
 
-    C v[19];
-    v[0] = exploded_self ? acc.coarse(brick, lx, ly, lz, 0) : acc.load(src, n, 0, cidx);
+// One sub-step of one level (Alg. 2 StreamCollide generalised to every level): pull stream with
+// boundary treatment, explosion reads and coalescence, then collide owned cells; ghost layers
+// 1-2 are streamed only.  Owned cells: each thread walks 2^lzc cells of one (x, y) column of a
+// brick; the 18 source offsets of a cell inside the brick are computed once per column, and a
+// per-cell link mask (read only where the column needs it) routes the few links that are not
+// plain same-level loads to pull_general.  CTAs after the owned part cover the ghost work list.
+template <typename T, typename C, int COLL, int LB, int MINB>
+__global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
+    constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
+    __shared__ C slow[19][256];
+    const int zc = 1 << a.lzc;
+    const int upb = (1 << B2s) << (LB - a.lzc);            // units (column chunks) per brick
+    const int64_t owned_units = int64_t(a.lv.nown) * upb;
+    const int64_t owned_ctas = (owned_units + 255) >> 8;
+    const void* src = a.lv.f[a.cur];
+    T* dst = static_cast<T*>(a.lv.f[a.cur ^ 1]);
+    const int64_t n = a.lv.ncells;
+    const Access<T, C> acc{a, LB, M};
+    const int tid = threadIdx.x;
+
+    if (int64_t(blockIdx.x) < owned_ctas) {
+        const int64_t u = int64_t(blockIdx.x) * 256 + tid;
+        if (u >= owned_units) return;
+        const int brick = int(u / upb);
+        const int r = int(u - int64_t(brick) * upb);
+        const int col = r & ((1 << B2s) - 1);
+        const int x = col & M, y = col >> LB;
+        const int z0 = (r >> B2s) << a.lzc;
+        const uint8_t bk = __ldg(a.lv.kind + brick);
+        const int* nbr = a.lv.nbr + brick * 27;
+        bool need_mask = !(bk & BK_PURE) || (bk & BK_TOUCH_FINER);
+        int off[19];
 #pragma unroll
-    for (int q = 1; q < 19; q++) {
-        const int ex = dex(q), ey = dey(q), ez = dez(q);
-        const int sx = lx - ex, sy = ly - ey, sz = lz - ez;
-        const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
-        const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
-        const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
-        const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
-        // coalescence: the PDF enters x from the finer level when the upwind cell along e_q, or
-        // along one axis component of e_q, lies in the finer level (fine-to-coarse, Sec. 4.4)
-        bool coal = false;
-        if (touch_finer) {
-            coal = nb == NB_FINER;
-            if (!coal && ex && ox) coal = __ldg(nbr + 13 + ox) == NB_FINER;
-            if (!coal && ey && oy) coal = __ldg(nbr + 13 + 3 * oy) == NB_FINER;
-            if (!coal && ez && oz) coal = __ldg(nbr + 13 + 9 * oz) == NB_FINER;
+        for (int q = 1; q < 19; q++) {
+            const int sx = x - dex(q), sy = y - dey(q);
+            const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+            const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+            const int nb = (ox | oy) ? __ldg(nbr + 13 + ox + 3 * oy) : brick;
+            if (nb < 0 || nb >= a.lv.nown || !(__ldg(a.lv.kind + nb) & BK_PURE)) need_mask = true;
+            off[q] = nb >= 0 ? (nb << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s) : 0;
         }
-        C val;
-        if (coal) {
-            val = acc.children_mean(brick, lx, ly, lz, q);
-        } else if (nb >= 0) {
-            const int tx = sx & M, ty = sy & M, tz = sz & M;
-            const int64_t sidx = (int64_t(nb) << B3s) + (tz << (2 * LB)) + (ty << LB) + tx;
-            if (__ldg(a.lv.kind + nb) & BK_PURE) {
-                val = acc.load(src, n, q, sidx);
-            } else {
-                const uint8_t ck = __ldg(a.lv.cell + sidx);
-                if (ck == CK_SOLID) {
-                    // no-slip bounce-back, pre-stream boundary treatment (Sec. 2.2)
-                    val = exploded_self ? acc.coarse(brick, lx, ly, lz, dopp(q)) : acc.load(src, n, dopp(q), cidx);
-                } else if (ck == CK_FLUID || (ck == CK_GHOST && a.substep == 2)) {
-                    val = acc.load(src, n, q, sidx);
-                } else {
-                    val = acc.coarse(nb, tx, ty, tz, q);
-                }
-            }
-        } else if (nb == NB_WALL) {
-            // domain wall: bounce-back, plus 6 w rho0 e.u_w on velocity walls; a cell beyond
-            // several faces takes the first of z+, z-, y+, y-, x+, x-
-            const int* P = a.lv.pos + 3 * brick;
-            const int gx = P[0] * B + sx, gy = P[1] * B + sy, gz = P[2] * B + sz;
-            int face;
-            if (!(a.per & 4) && gz >= a.lv.N[2]) face = 5;
-            else if (!(a.per & 4) && gz < 0) face = 4;
-            else if (!(a.per & 2) && gy >= a.lv.N[1]) face = 3;
-            else if (!(a.per & 2) && gy < 0) face = 2;
-            else if (!(a.per & 1) && gx >= a.lv.N[0]) face = 1;
-            else face = 0;
-            const C own = exploded_self ? acc.coarse(brick, lx, ly, lz, dopp(q)) : acc.load(src, n, dopp(q), cidx);
-            val = own + C(a.wall[face * 19 + q]);
-        } else {
-            val = qnan<C>();
-        }
-        v[q] = val;
-    }
-    void* dstv = a.lv.f[a.cur ^ 1];
-    T* dst = static_cast<T*>(dstv);
-    if (!ghost) {
         const LevelParams* P = a.params;
-        C F[19];
+        const C le = Par<C>::le(P), lo = Par<C>::lo(P);
+        const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
+        const C rho0 = C(a.rho0), inv_rho0 = C(a.inv_rho0);
+        constexpr uint32_t ZLO = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);   // e_z = +1
+        constexpr uint32_t ZHI = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);   // e_z = -1
+        for (int k = 0; k < zc; k++) {
+            const int z = z0 + k;
+            const int zoff = z << B2s;
+            const int cidx = (brick << B3s) + zoff + (y << LB) + x;
+            uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
+            if (m & LINK_NOT_FLUID) continue;
+            if (z == 0) m |= ZLO;
+            if (z == M) m |= ZHI;
+            C v[19];
+            v[0] = acc.load(src, n, 0, cidx);
 #pragma unroll
-        for (int q = 0; q < 19; q++) F[q] = C(P->force[q]);
-        collide<C, COLL>(v, C(P->le), C(P->lo), F, C(a.rho0), C(1.0 / a.rho0));
+            for (int q = 1; q < 19; q++) v[q] = ((m >> q) & 1u) ? C(0) : acc.load(src, n, q, off[q] + zoff);
+            if (m) {
+                for (int q = 1; q < 19; q++)
+                    if ((m >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
+#pragma unroll
+                for (int q = 1; q < 19; q++)
+                    if ((m >> q) & 1u) v[q] = slow[q][tid];
+            }
+            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0);
+#pragma unroll
+            for (int q = 0; q < 19; q++) Store<T>::st(dst + int64_t(q) * n + cidx, v[q]);
+        }
+        return;
     }
-#pragma unroll
-    for (int q = 0; q < 19; q++) Store<T>::st(dst + int64_t(q) * n + cidx, v[q]);
+    // ghost layers 1-2: stream only
+    const int i = int(int64_t(blockIdx.x - owned_ctas) * 256 + tid);
+    if (i >= a.lv.ngcells) return;
+    const int c = __ldg(a.lv.gcells + i);
+    const int brick = c >> B3s, local = c & ((1 << B3s) - 1);
+    const int x = local & M, y = (local >> LB) & M, z = local >> B2s;
+    for (int q = 0; q < 19; q++) {
+        C val;
+        if (q == 0) val = a.substep == 1 ? acc.coarse(brick, x, y, z, 0) : acc.load(src, n, 0, c);
+        else val = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
+        Store<T>::st(dst + int64_t(q) * n + c, val);
+    }
 }
 
 // Equilibrium start (Eq. fequ) followed by one collision, so the stored state is post-collision.
@@ -285,10 +343,8 @@ __global__ void init_kernel(const DevLevel lv, int cur, int LB, const LevelParam
         const double R = Store<T>::shifted ? r - rho0 : r;
         v[q] = C(dw(q) * (R + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
     }
-    C F[19];
-#pragma unroll
-    for (int q = 0; q < 19; q++) F[q] = C(P->force[q]);
-    collide<C, COLL>(v, C(P->le), C(P->lo), F, C(rho0), C(1.0 / rho0));
+    const C fa[3] = {C(P->fa[0]), C(P->fa[1]), C(P->fa[2])};
+    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0));
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         Store<T>::st(f + q * lv.ncells + i, v[q]);

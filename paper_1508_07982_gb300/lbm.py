@@ -27,7 +27,7 @@ EXPORTS = [
     "lbm_get_block_table", "lbm_cell_updates_per_coarse_step", "lbm_set_level_params",
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
-    "lbm_launches_per_coarse_step",
+    "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
 ]
 
 
@@ -96,6 +96,8 @@ def library():
             "lbm_timing_begin": [P, ctypes.c_int32],
             "lbm_timing_end": [P, dp, i64p],
             "lbm_launches_per_coarse_step": [P, i32p],
+            "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
+            "lbm_get_kernel_config": [P, i32p, i32p],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -336,6 +338,14 @@ class Forest:
         out = np.zeros(4)
         _check(library().lbm_reduce_mass_momentum(self.h, _dp(out)))
         return out
+
+    def set_kernel_config(self, cells_per_thread_log2, ctas_per_sm):
+        _check(library().lbm_set_kernel_config(self.h, cells_per_thread_log2, ctas_per_sm))
+
+    def kernel_config(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(library().lbm_get_kernel_config(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def timing_begin(self, max_steps):
         _check(library().lbm_timing_begin(self.h, max_steps))

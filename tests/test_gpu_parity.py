@@ -213,3 +213,21 @@ def test_timing_api_reports_every_launch(lbm):
     assert cnt.tolist() == [5, 10]
     assert (ms > 0).all()
     assert f.launches_per_coarse_step() == 3
+
+
+def test_thread_mapping_does_not_change_results(lbm):
+    """Every (cells per thread, CTAs per SM) variant of the step kernel computes each cell the same
+    way, so the PDFs agree bit for bit."""
+    case = inputs.sphere_channel_case(H=32, B=16, radii=(20.0, 12.0, 6.5))
+    ref = None
+    for lzc, minb in ((0, 3), (2, 3), (4, 2), (1, 2)):
+        f = lbm.Forest(case, precision="fp32s")
+        f.set_kernel_config(lzc, minb)
+        f.init_uniform(case["u_init"])
+        f.step_coarse(3)
+        out = [f.get_pdfs(L) for L in range(f.nlev)]
+        if ref is None:
+            ref = out
+        else:
+            for L in range(f.nlev):
+                assert np.array_equal(out[L], ref[L], equal_nan=True)
