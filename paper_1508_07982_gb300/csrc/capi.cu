@@ -55,6 +55,7 @@ struct DevBuf {
     int32_t *nbr = nullptr, *parent = nullptr, *child = nullptr, *pos = nullptr, *gcells = nullptr;
     uint8_t* kind = nullptr;
     uint32_t* link = nullptr;
+    uint32_t* glink = nullptr;
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -114,6 +115,7 @@ struct lbm_forest {
     int64_t updates = 0;
     int lzc = 3;        // log2 of the cells per thread along z in the owned part of the step kernel
     int minb = 3;       // CTAs per SM of the step-kernel variant
+    bool explode_pending = true;   // ghost layers must be exploded from the coarser level
 };
 
 namespace {
@@ -232,6 +234,16 @@ lbm_status capture(lbm_forest* f, int timed, int parity) {
     return LBM_OK;
 }
 
+// Fills ghost layers 1-4 of every level from its coarser level (Eq. ctof); the step kernels keep
+// them up to date afterwards by pushing the explosion from the coarse side.
+lbm_status explode_all(lbm_forest* f) {
+    for (int L = 1; L < f->plan.nlev; L++)
+        f->L->explode(f->dl[L], f->dl[L - 1], f->cur[L], f->cur[L - 1], f->plan.LB, f->stream);
+    CU(cudaGetLastError());
+    f->explode_pending = false;
+    return LBM_OK;
+}
+
 lbm_status ensure_stage(lbm_forest* f, size_t bytes) {
     if (f->stage_bytes >= bytes) return LBM_OK;
     if (f->d_stage) cudaFree(f->d_stage);
@@ -341,6 +353,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.gcells);
         cudaFree(b.kind);
         cudaFree(b.link);
+        cudaFree(b.glink);
     }
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
@@ -390,7 +403,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         lbm_status s;
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
-            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)))
+            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)))
             return bail(s);
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -403,6 +416,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.kind = b.kind;
         g.gcells = b.gcells;
         g.link = b.link;
+        g.glink = b.glink;
         g.nown = V.nown;
         g.nbricks = V.nbricks();
         g.ngcells = int(V.gcells.size());
@@ -433,8 +447,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
         cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
         return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
-    // cells per thread along z: 8 for 32^3 blocks, 4 for 16^3, 2 for 8^3
-    f->lzc = P.LB - 2;
+    // cells per thread along z: 4 for 32^3 blocks, 2 for 16^3, 1 for 8^3
+    f->lzc = P.LB - 3;
     build_schedule(f);
     *out = f;
     return LBM_OK;
@@ -515,6 +529,7 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
         }
         CU(cudaGetLastError());
         f->init_mask = (1u << P.nlev) - 1;
+        f->explode_pending = true;
         return LBM_OK;
     }
     lbm_status s = check_level(f, level);
@@ -535,6 +550,7 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
+    f->explode_pending = true;
     return LBM_OK;
 }
 
@@ -543,6 +559,10 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
     if (n_steps < 0) return fail(LBM_EINVAL, "negative step count");
     if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
         return fail(LBM_EINVAL, "set the level parameters and initialise every level before stepping");
+    if (f->explode_pending) {
+        lbm_status s = explode_all(f);
+        if (s) return s;
+    }
     for (int i = 0; i < n_steps; i++) {
         const int p = f->cur[0];
         const int timed = f->timing && f->tused < f->tmax ? 1 : 0;
@@ -621,6 +641,7 @@ lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
+    f->explode_pending = true;
     return LBM_OK;
 }
 

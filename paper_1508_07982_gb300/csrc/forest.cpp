@@ -260,47 +260,81 @@ struct Builder {
                         int g[3] = {P[0] * B + x, P[1] * B + y, P[2] * B + z};
                         uint8_t ck;
                         if (obstacle(L - 1, g[0] >> 1, g[1] >> 1, g[2] >> 1)) ck = CK_SOLID;
-                        else ck = dmin <= 2 ? CK_GHOST : CK_FAR;
+                        else ck = dmin <= 2 ? CK_GHOST : (dmin <= 4 ? CK_G34 : CK_FAR);
                         int c = (z * B + y) * B + x;
                         cells[c] = ck;
                         if (ck == CK_GHOST) V.gcells.push_back(int32_t(size_t(k) * B3 + c));
                     }
+            // a ghost brick without obstacle cells: every source in it is a stored value
+            bool pure = true;
+            for (int c = 0; c < B3 && pure; c++) pure = cells[c] != CK_SOLID;
+            if (pure) V.kind[k] |= BK_PURE;
         }
         return true;
     }
 
-    // Per owned cell: which of the 18 pulls need the general path (source not an owned fluid
-    // cell of this level, or a PDF that coalescence replaces), and whether the cell is fluid.
+    // Link bits of cell (x, y, z) of brick k: bit q is set when pull q is not a plain load of a
+    // stored value of this level (the source is an obstacle or lies beyond a wall, or, for owned
+    // cells, coalescence replaces the PDF).  With the explosion written into ghost layers 1-4 by
+    // the coarser level, sources in ghost layers are stored values.
+    uint32_t link_bits(const HostLevel& V, int k, int x, int y, int z, bool owned) const {
+        const int B = p.B, B3 = B * B * B, M = B - 1;
+        const int32_t* nbr = &V.nbr[size_t(k) * 27];
+        const bool finer = owned && (V.kind[k] & BK_TOUCH_FINER);
+        uint32_t m = 0;
+        for (int q = 1; q < Q; q++) {
+            int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
+            for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
+            int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
+            bool plain = false;
+            if (nb >= 0) {
+                uint8_t ck = V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)];
+                plain = ck == CK_FLUID || ck == CK_GHOST || ck == CK_G34;
+            }
+            if (finer) {
+                bool coal = nb == NB_FINER;
+                if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
+                if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
+                if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
+                if (coal) plain = false;
+            }
+            if (!plain) m |= 1u << q;
+        }
+        return m;
+    }
+
+    // Owned cells: link bits, bit 31 for non-fluid cells, and the explosion code in bits 29-30:
+    // 1 when the cell's 8 children on level L+1 are fluid ghost cells of layers 1-2, 2 when they
+    // are of layers 3-4 (Eq. ctof pushes the post-collision value into them).  Ghost work list:
+    // link bits only.
     void links(int L) {
         HostLevel& V = p.lv[L];
-        const int B = p.B, B3 = B * B * B, M = B - 1;
+        const int B = p.B, B3 = B * B * B;
         V.link.assign(size_t(V.nown) * B3, 0u);
-        for (int k = 0; k < V.nown; k++) {
-            const int32_t* nbr = &V.nbr[size_t(k) * 27];
-            const bool finer = V.kind[k] & BK_TOUCH_FINER;
+        const HostLevel* F = L + 1 < p.nlev ? &p.lv[L + 1] : nullptr;
+        for (int k = 0; k < V.nown; k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
                     for (int x = 0; x < B; x++) {
                         const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
-                        uint32_t m = 0;
+                        uint32_t m = link_bits(V, k, x, y, z, true);
                         if (V.cell[c] != CK_FLUID) m |= 1u << 31;
-                        for (int q = 1; q < Q; q++) {
-                            int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
-                            for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
-                            int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
-                            bool plain = nb >= 0 && nb < V.nown &&
-                                         V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] == CK_FLUID;
-                            if (plain && finer) {
-                                bool coal = nb == NB_FINER;
-                                if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
-                                if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
-                                if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
-                                plain = !coal;
+                        if (F && V.cell[c] == CK_FLUID) {
+                            const int oct = ((2 * x) / B) | (((2 * y) / B) << 1) | (((2 * z) / B) << 2);
+                            const int32_t cb = V.child[size_t(k) * 8 + oct];
+                            if (cb >= 0) {
+                                const int cx = (2 * x) % B, cy = (2 * y) % B, cz = (2 * z) % B;
+                                const uint8_t ck = F->cell[size_t(cb) * B3 + (size_t(cz) * B + cy) * B + cx];
+                                if (ck == CK_GHOST) m |= 1u << 29;
+                                else if (ck == CK_G34) m |= 2u << 29;
                             }
-                            if (!plain) m |= 1u << q;
                         }
                         V.link[c] = m;
                     }
+        V.glink.resize(V.gcells.size());
+        for (size_t i = 0; i < V.gcells.size(); i++) {
+            const int c = V.gcells[i], k = c / B3, r = c % B3;
+            V.glink[i] = link_bits(V, k, r % B, (r / B) % B, r / (B * B), false);
         }
     }
 

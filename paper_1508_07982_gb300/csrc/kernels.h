@@ -28,7 +28,8 @@ struct DevLevel {
     const uint8_t* kind;  // [nbricks]
     const int32_t* gcells;
     const uint32_t* link; // [nown * B^3] per owned cell: bit q set = link q needs the general pull;
-                          // bit 31 = the cell is not a fluid cell
+                          // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
+    const uint32_t* glink;  // [ngcells] link bits of the ghost work list
     int nown, nbricks, ngcells;
     int64_t ncells;
     int N[3];
@@ -49,6 +50,7 @@ struct StepArgs {
 
 // Bits of the per-cell link mask.
 constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
+constexpr uint32_t LINK_EXPLODE = 3u << 29;
 constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18
 
 // Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).
@@ -62,6 +64,7 @@ struct Launchers {
     void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
                    int grid, cudaStream_t s);
+    void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int LB, cudaStream_t s);
 };
 const Launchers& launchers_f64();
 const Launchers& launchers_f32();

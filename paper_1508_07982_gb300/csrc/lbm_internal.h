@@ -20,8 +20,9 @@ inline double weight(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 :
 enum : uint8_t {
     CK_FLUID = 0,  // owned fluid cell: collides and streams
     CK_GHOST = 1,  // fluid cell of ghost layers 1-2 (covered by the coarser level): streams only
-    CK_FAR = 2,    // fluid cell of ghost layers 3+ : never streamed, read from the coarse parent
+    CK_FAR = 2,    // fluid cell of ghost layer 5 or beyond: never read
     CK_SOLID = 3,  // no-slip obstacle
+    CK_G34 = 4,    // fluid cell of ghost layers 3-4: holds the exploded coarse value, never streamed
 };
 // Neighbour-table codes for block positions that hold no brick of this level.
 enum : int32_t { NB_WALL = -1, NB_FINER = -2, NB_COARSE = -3 };
@@ -40,7 +41,8 @@ struct HostLevel {
     std::vector<uint8_t> cell;     // [nbricks * B^3] CK_* per cell
     std::vector<int32_t> gcells;   // cell indices of CK_GHOST cells (the ghost work list)
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
-                                   // same-level load; bit 31 = not a fluid cell
+                                   // same-level load; bits 29-30 = explosion code; bit 31 = not fluid
+    std::vector<uint32_t> glink;   // [gcells] the same link bits for the ghost work list
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }
 };

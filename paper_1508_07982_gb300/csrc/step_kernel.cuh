@@ -117,16 +117,6 @@ struct Access {
     __device__ __forceinline__ C load(const void* base, int64_t n, int q, int64_t idx) const {
         return C(Store<T>::ld(static_cast<const T*>(base) + int64_t(q) * n + idx));
     }
-    // Value of the coarse parent of cell (x, y, z) of ghost brick g (explosion, Eq. ctof).
-    __device__ __forceinline__ C coarse(int g, int x, int y, int z, int q) const {
-        const int pk = __ldg(a.lv.parent + g);
-        if (pk < 0) return qnan<C>();
-        const int pb = pk >> 3, oct = pk & 7;
-        const int B = 1 << LB;
-        const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1, pz = ((oct >> 2) * B + z) >> 1;
-        const int64_t idx = (int64_t(pb) << (3 * LB)) + (pz << (2 * LB)) + (py << LB) + px;
-        return load(a.co.f[a.cur_c], a.co.ncells, q, idx);
-    }
     // Mean of the 8 finer children of owned cell (x, y, z) of brick b after both fine sub-steps
     // (coalescence, Eq. ftoc), summed pairwise in FP64 in z-y-x bit order.
     __device__ __forceinline__ C children_mean(int b, int x, int y, int z, int q) const {
@@ -164,18 +154,17 @@ template <> struct Par<float> {
     __device__ __forceinline__ static float fa(const LevelParams* P, int k) { return P->faf[k]; }
 };
 
-// General pull of direction q into cell (x, y, z) of brick `brick` (owned or ghost): neighbour
-// lookup through the 27-entry table, then by the class of the source cell
-//   - coalescence (owned x only): mean of the 8 finer children of x (Eq. ftoc);
-//   - obstacle or domain wall: bounce-back of the own opposite value (Sec. 2.2), plus the
-//     velocity term on velocity walls; a cell beyond several faces takes the first of
+// General pull of direction q into cell (x, y, z) of brick `brick` (owned or ghost), for the
+// links the link mask routes here:
+//   - coalescence (owned cells only): mean of the 8 finer children of x (Eq. ftoc);
+//   - obstacle or domain wall: bounce-back of the cell's own opposite value (Sec. 2.2), plus
+//     6 w rho0 e.u_w on velocity walls; a source beyond several faces takes the first of
 //     z+, z-, y+, y-, x+, x-;
-//   - owned fluid, or ghost layer 1-2 in the second sub-step: the stored value;
-//   - ghost layer 1-2 in the first sub-step, or ghost layer 3+: the coarse parent (Eq. ctof).
-// In the first sub-step a ghost cell's own value is its coarse parent as well.
+//   - otherwise the stored value of the source cell (owned, or ghost layers 1-4, which hold the
+//     exploded coarse values or their first-sub-step stream).
 template <typename T, typename C, int LB>
 __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick, int x, int y, int z, int q,
-                          bool ghost) {
+                          bool owned) {
     constexpr int B = 1 << LB, M = B - 1, B3s = 3 * LB;
     const int ex = dex(q), ey = dey(q), ez = dez(q);
     const int sx = x - ex, sy = y - ey, sz = z - ez;
@@ -187,8 +176,7 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     const void* src = a.lv.f[a.cur];
     const int64_t n = a.lv.ncells;
     const int64_t cidx = (int64_t(brick) << B3s) + (z << (2 * LB)) + (y << LB) + x;
-    const bool exploded_self = ghost && a.substep == 1;
-    if (!ghost && (__ldg(a.lv.kind + brick) & BK_TOUCH_FINER)) {
+    if (owned && (__ldg(a.lv.kind + brick) & BK_TOUCH_FINER)) {
         bool coal = nb == NB_FINER;
         if (!coal && ex && ox) coal = __ldg(nbr + 13 + ox) == NB_FINER;
         if (!coal && ey && oy) coal = __ldg(nbr + 13 + 3 * oy) == NB_FINER;
@@ -197,13 +185,11 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     }
     const int qo = dopp(q);
     if (nb >= 0) {
-        const int tx = sx & M, ty = sy & M, tz = sz & M;
-        const int64_t sidx = (int64_t(nb) << B3s) + (tz << (2 * LB)) + (ty << LB) + tx;
-        const uint8_t ck = (__ldg(a.lv.kind + nb) & BK_PURE) ? uint8_t(CK_FLUID) : __ldg(a.lv.cell + sidx);
-        if (ck == CK_SOLID)
-            return exploded_self ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
-        if (ck == CK_FLUID || (ck == CK_GHOST && a.substep == 2)) return acc.load(src, n, q, sidx);
-        return acc.coarse(nb, tx, ty, tz, q);
+        const int64_t sidx = (int64_t(nb) << B3s) + ((sz & M) << (2 * LB)) + ((sy & M) << LB) + (sx & M);
+        const uint8_t ck = __ldg(a.lv.cell + sidx);
+        if (ck == CK_SOLID) return acc.load(src, n, qo, cidx);
+        if (ck == CK_FAR) return qnan<C>();
+        return acc.load(src, n, q, sidx);
     }
     if (nb == NB_WALL) {
         const int* P = a.lv.pos + 3 * brick;
@@ -215,18 +201,44 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
         else if (!(a.per & 2) && gy < 0) face = 2;
         else if (!(a.per & 1) && gx >= a.lv.N[0]) face = 1;
         else face = 0;
-        const C own = exploded_self ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
-        return own + C(__ldg(a.wall + face * 19 + q));
+        return acc.load(src, n, qo, cidx) + C(__ldg(a.wall + face * 19 + q));
     }
     return qnan<C>();
 }
 
+// Explosion (Eq. ctof) pushed from the coarse side: the post-collision value v of owned cell
+// (x, y, z) of brick `brick` goes to its 8 children on the next finer level.  Children in ghost
+// layers 1-2 (code 1) are written to the finer level's current grid, which its next first
+// sub-step reads; children in layers 3-4 (code 2), never streamed, are written to both grids.
+template <typename T, typename C, int LB>
+__device__ __forceinline__ void explode_children(const StepArgs& a, int brick, int x, int y, int z, int code,
+                                                 const C (&v)[19]) {
+    constexpr int B = 1 << LB, M = B - 1, B3s = 3 * LB;
+    const int oct = ((2 * x) >> LB) | (((2 * y) >> LB) << 1) | (((2 * z) >> LB) << 2);
+    const int cb = __ldg(a.lv.child + brick * 8 + oct);
+    if (cb < 0) return;
+    const int cx = (2 * x) & M, cy = (2 * y) & M, cz = (2 * z) & M;
+    const int64_t base = (int64_t(cb) << B3s) + (cz << (2 * LB)) + (cy << LB) + cx;
+    const int64_t nf = a.fi.ncells;
+    T* g0 = static_cast<T*>(a.fi.f[a.cur_f]);
+    T* g1 = static_cast<T*>(a.fi.f[a.cur_f ^ 1]);
+    for (int j = 0; j < 8; j++) {
+        const int64_t idx = base + ((j >> 2) << (2 * LB)) + (((j >> 1) & 1) << LB) + (j & 1);
+#pragma unroll
+        for (int q = 0; q < 19; q++) {
+            Store<T>::st(g0 + int64_t(q) * nf + idx, v[q]);
+            if (code == 2) Store<T>::st(g1 + int64_t(q) * nf + idx, v[q]);
+        }
+    }
+}
+
 // One sub-step of one level (Alg. 2 StreamCollide generalised to every level): pull stream with
-// boundary treatment, explosion reads and coalescence, then collide owned cells; ghost layers
-// 1-2 are streamed only.  Owned cells: each thread walks 2^lzc cells of one (x, y) column of a
-// brick; the 18 source offsets of a cell inside the brick are computed once per column, and a
-// per-cell link mask (read only where the column needs it) routes the few links that are not
-// plain same-level loads to pull_general.  CTAs after the owned part cover the ghost work list.
+// boundary treatment and coalescence, collide owned cells, push the explosion into the finer
+// level's ghost layers; ghost layers 1-2 of this level are streamed only.  Owned cells: each
+// thread walks 2^lzc cells of one (x, y) column of a brick; the source offsets of a cell inside
+// the brick are computed once per column, and a per-cell link mask (read where the column needs
+// it) routes the few links that are not plain loads to pull_general.  CTAs after the owned part
+// cover the ghost work list.
 template <typename T, typename C, int COLL, int LB, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
@@ -235,11 +247,13 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     const int upb = (1 << B2s) << (LB - a.lzc);            // units (column chunks) per brick
     const int64_t owned_units = int64_t(a.lv.nown) * upb;
     const int64_t owned_ctas = (owned_units + 255) >> 8;
-    const void* src = a.lv.f[a.cur];
+    const T* src = static_cast<const T*>(a.lv.f[a.cur]);
     T* dst = static_cast<T*>(a.lv.f[a.cur ^ 1]);
     const int64_t n = a.lv.ncells;
     const Access<T, C> acc{a, LB, M};
     const int tid = threadIdx.x;
+    constexpr uint32_t ZLO = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);   // e_z = +1
+    constexpr uint32_t ZHI = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);   // e_z = -1
 
     if (int64_t(blockIdx.x) < owned_ctas) {
         const int64_t u = int64_t(blockIdx.x) * 256 + tid;
@@ -259,51 +273,115 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
             const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
             const int nb = (ox | oy) ? __ldg(nbr + 13 + ox + 3 * oy) : brick;
-            if (nb < 0 || nb >= a.lv.nown || !(__ldg(a.lv.kind + nb) & BK_PURE)) need_mask = true;
+            if (nb < 0 || !(__ldg(a.lv.kind + nb) & BK_PURE)) need_mask = true;
             off[q] = nb >= 0 ? (nb << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s) : 0;
         }
         const LevelParams* P = a.params;
         const C le = Par<C>::le(P), lo = Par<C>::lo(P);
         const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
         const C rho0 = C(a.rho0), inv_rho0 = C(a.inv_rho0);
-        constexpr uint32_t ZLO = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);   // e_z = +1
-        constexpr uint32_t ZHI = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);   // e_z = -1
         for (int k = 0; k < zc; k++) {
             const int z = z0 + k;
             const int zoff = z << B2s;
             const int cidx = (brick << B3s) + zoff + (y << LB) + x;
             uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
             if (m & LINK_NOT_FLUID) continue;
-            if (z == 0) m |= ZLO;
-            if (z == M) m |= ZHI;
+            uint32_t mq = m & LINK_ALL;
+            if (z == 0) mq |= ZLO;
+            if (z == M) mq |= ZHI;
             C v[19];
-            v[0] = acc.load(src, n, 0, cidx);
+            {
+                const T* p = src;
+                v[0] = C(Store<T>::ld(p + cidx));
 #pragma unroll
-            for (int q = 1; q < 19; q++) v[q] = ((m >> q) & 1u) ? C(0) : acc.load(src, n, q, off[q] + zoff);
-            if (m) {
+                for (int q = 1; q < 19; q++) {
+                    p += n;
+                    v[q] = ((mq >> q) & 1u) ? C(0) : C(Store<T>::ld(p + (off[q] + zoff)));
+                }
+            }
+            if (mq) {
                 for (int q = 1; q < 19; q++)
-                    if ((m >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
+                    if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
 #pragma unroll
                 for (int q = 1; q < 19; q++)
-                    if ((m >> q) & 1u) v[q] = slow[q][tid];
+                    if ((mq >> q) & 1u) v[q] = slow[q][tid];
             }
             collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0);
+            {
+                T* p = dst + cidx;
 #pragma unroll
-            for (int q = 0; q < 19; q++) Store<T>::st(dst + int64_t(q) * n + cidx, v[q]);
+                for (int q = 0; q < 19; q++) {
+                    Store<T>::st(p, v[q]);
+                    p += n;
+                }
+            }
+            if (m & LINK_EXPLODE) explode_children<T, C, LB>(a, brick, x, y, z, int((m & LINK_EXPLODE) >> 29), v);
         }
         return;
     }
-    // ghost layers 1-2: stream only
+    // ghost layers 1-2: stream only; sources are stored values except where the link mask says
     const int i = int(int64_t(blockIdx.x - owned_ctas) * 256 + tid);
     if (i >= a.lv.ngcells) return;
     const int c = __ldg(a.lv.gcells + i);
+    const uint32_t mq = __ldg(a.lv.glink + i);
     const int brick = c >> B3s, local = c & ((1 << B3s) - 1);
     const int x = local & M, y = (local >> LB) & M, z = local >> B2s;
+    const int* nbr = a.lv.nbr + brick * 27;
+    C v[19];
+    {
+        const T* p = src;
+        v[0] = C(Store<T>::ld(p + c));
+#pragma unroll
+        for (int q = 1; q < 19; q++) {
+            p += n;
+            const int sx = x - dex(q), sy = y - dey(q), sz = z - dez(q);
+            const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+            const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+            const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
+            const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
+            const int sidx = (max(nb, 0) << B3s) + ((sz & M) << B2s) + ((sy & M) << LB) + (sx & M);
+            v[q] = ((mq >> q) & 1u) ? C(0) : C(Store<T>::ld(p + sidx));
+        }
+    }
+    if (mq) {
+        for (int q = 1; q < 19; q++)
+            if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
+#pragma unroll
+        for (int q = 1; q < 19; q++)
+            if ((mq >> q) & 1u) v[q] = slow[q][tid];
+    }
+    T* p = dst + c;
+#pragma unroll
     for (int q = 0; q < 19; q++) {
-        C val;
-        if (q == 0) val = a.substep == 1 ? acc.coarse(brick, x, y, z, 0) : acc.load(src, n, 0, c);
-        else val = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
-        Store<T>::st(dst + int64_t(q) * n + c, val);
+        Store<T>::st(p, v[q]);
+        p += n;
+    }
+}
+
+// Explosion of a whole level from its coarser level (Eq. ctof), used after the state is set from
+// outside (initial equilibrium, checkpoint): every fluid cell of ghost layers 1-4 takes its coarse
+// parent's value, in the current grid, and layers 3-4 in both grids.
+template <typename T>
+__global__ void explode_level_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c, int LB) {
+    const int B3s = 3 * LB, M = (1 << LB) - 1;
+    const int64_t first = int64_t(lv.nown) << B3s;
+    const int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= lv.ncells) return;
+    const uint8_t ck = lv.cell[i];
+    if (ck != CK_GHOST && ck != CK_G34) return;
+    const int g = int(i >> B3s), local = int(i & ((int64_t(1) << B3s) - 1));
+    const int x = local & M, y = (local >> LB) & M, z = local >> (2 * LB);
+    const int pk = lv.parent[g];
+    const int pb = pk >> 3, oct = pk & 7, B = 1 << LB;
+    const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1, pz = ((oct >> 2) * B + z) >> 1;
+    const int64_t pidx = (int64_t(pb) << B3s) + (pz << (2 * LB)) + (py << LB) + px;
+    const T* cf = static_cast<const T*>(co.f[cur_c]);
+    T* f0 = static_cast<T*>(lv.f[cur]);
+    T* f1 = static_cast<T*>(lv.f[cur ^ 1]);
+    for (int q = 0; q < 19; q++) {
+        const T v = cf[q * co.ncells + pidx];
+        f0[q * lv.ncells + i] = v;
+        if (ck == CK_G34) f1[q * lv.ncells + i] = v;
     }
 }
 
