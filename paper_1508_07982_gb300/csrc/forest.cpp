@@ -310,6 +310,14 @@ struct Builder {
     void links(int L) {
         HostLevel& V = p.lv[L];
         const int B = p.B, B3 = B * B * B;
+        for (int k = 0; k < V.nown; k++) {
+            bool plain = (V.kind[k] & BK_PURE) && !(V.kind[k] & BK_TOUCH_FINER);
+            for (int o = 0; o < 27 && plain; o++) {
+                const int32_t nb = V.nbr[size_t(k) * 27 + o];
+                plain = nb >= 0 && (V.kind[nb] & BK_PURE);
+            }
+            if (plain) V.kind[k] |= BK_PLAIN;
+        }
         V.link.assign(size_t(V.nown) * B3, 0u);
         const HostLevel* F = L + 1 < p.nlev ? &p.lv[L + 1] : nullptr;
         for (int k = 0; k < V.nown; k++)

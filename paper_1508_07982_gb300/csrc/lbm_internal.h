@@ -27,7 +27,9 @@ enum : uint8_t {
 // Neighbour-table codes for block positions that hold no brick of this level.
 enum : int32_t { NB_WALL = -1, NB_FINER = -2, NB_COARSE = -3 };
 // Brick attribute bits.
-enum : uint8_t { BK_PURE = 1, BK_TOUCH_FINER = 2, BK_GHOST = 4 };
+// BK_PURE: no obstacle cell.  BK_PLAIN (owned bricks): every pull of every cell is a plain load of a
+// stored value (pure, no finer neighbour, all 26 neighbours present and pure).
+enum : uint8_t { BK_PURE = 1, BK_TOUCH_FINER = 2, BK_GHOST = 4, BK_PLAIN = 8 };
 
 struct HostLevel {
     int N[3] = {0, 0, 0};    // cells per axis on this level

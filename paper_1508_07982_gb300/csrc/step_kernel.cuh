@@ -252,8 +252,6 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     const int64_t n = a.lv.ncells;
     const Access<T, C> acc{a, LB, M};
     const int tid = threadIdx.x;
-    constexpr uint32_t ZLO = (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18);   // e_z = +1
-    constexpr uint32_t ZHI = (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17);   // e_z = -1
 
     if (int64_t(blockIdx.x) < owned_ctas) {
         const int64_t u = int64_t(blockIdx.x) * 256 + tid;
@@ -265,7 +263,8 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
         const int z0 = (r >> B2s) << a.lzc;
         const uint8_t bk = __ldg(a.lv.kind + brick);
         const int* nbr = a.lv.nbr + brick * 27;
-        bool need_mask = !(bk & BK_PURE) || (bk & BK_TOUCH_FINER);
+        const bool need_mask = !(bk & BK_PLAIN);
+        // source offsets of a cell inside the brick along z (in-plane neighbour bricks resolved)
         int off[19];
 #pragma unroll
         for (int q = 1; q < 19; q++) {
@@ -273,8 +272,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
             const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
             const int nb = (ox | oy) ? __ldg(nbr + 13 + ox + 3 * oy) : brick;
-            if (nb < 0 || !(__ldg(a.lv.kind + nb) & BK_PURE)) need_mask = true;
-            off[q] = nb >= 0 ? (nb << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s) : 0;
+            off[q] = (max(nb, 0) << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s);
         }
         const LevelParams* P = a.params;
         const C le = Par<C>::le(P), lo = Par<C>::lo(P);
@@ -284,11 +282,10 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int z = z0 + k;
             const int zoff = z << B2s;
             const int cidx = (brick << B3s) + zoff + (y << LB) + x;
-            uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
-            if (m & LINK_NOT_FLUID) continue;
-            uint32_t mq = m & LINK_ALL;
-            if (z == 0) mq |= ZLO;
-            if (z == M) mq |= ZHI;
+            // The loads do not wait for the link mask: every address below lies inside the level's
+            // grid, and the links the mask marks are replaced afterwards.  On the brick's z faces
+            // the links that leave the brick read the z-neighbour brick (z is uniform in a warp).
+            const uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
             C v[19];
             {
                 const T* p = src;
@@ -296,9 +293,19 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
 #pragma unroll
                 for (int q = 1; q < 19; q++) {
                     p += n;
-                    v[q] = ((mq >> q) & 1u) ? C(0) : C(Store<T>::ld(p + (off[q] + zoff)));
+                    int s = off[q] + zoff;
+                    if ((dez(q) == 1 && z == 0) || (dez(q) == -1 && z == M)) {
+                        const int sx = x - dex(q), sy = y - dey(q), oz = dez(q) == 1 ? -1 : 1;
+                        const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+                        const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+                        const int nb = __ldg(nbr + 13 + ox + 3 * oy + 9 * oz);
+                        s = (max(nb, 0) << B3s) + ((oz < 0 ? M : 0) << B2s) + ((sy & M) << LB) + (sx & M);
+                    }
+                    v[q] = C(Store<T>::ld(p + s));
                 }
             }
+            if (m & LINK_NOT_FLUID) continue;
+            const uint32_t mq = m & LINK_ALL;
             if (mq) {
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
@@ -323,7 +330,6 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     const int i = int(int64_t(blockIdx.x - owned_ctas) * 256 + tid);
     if (i >= a.lv.ngcells) return;
     const int c = __ldg(a.lv.gcells + i);
-    const uint32_t mq = __ldg(a.lv.glink + i);
     const int brick = c >> B3s, local = c & ((1 << B3s) - 1);
     const int x = local & M, y = (local >> LB) & M, z = local >> B2s;
     const int* nbr = a.lv.nbr + brick * 27;
@@ -340,9 +346,10 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
             const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
             const int sidx = (max(nb, 0) << B3s) + ((sz & M) << B2s) + ((sy & M) << LB) + (sx & M);
-            v[q] = ((mq >> q) & 1u) ? C(0) : C(Store<T>::ld(p + sidx));
+            v[q] = C(Store<T>::ld(p + sidx));
         }
     }
+    const uint32_t mq = __ldg(a.lv.glink + i);
     if (mq) {
         for (int q = 1; q < 19; q++)
             if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
