@@ -149,13 +149,13 @@ def _run_timed(lbm, torch, case, precision, steps, warmup, timing=True):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    lev = f.timing_end() if timing else None
+    lev = f.timing_end(explode=True) if timing else None
     return f, ms, lev
 
 
 def _roofline(f, lev, precision, peaks, peak_kind):
-    ms_l, cnt_l = lev
-    share = ms_l / ms_l.sum()
+    ms_l, cnt_l, ems_l, ecnt_l = lev
+
     L = int(np.argmax(ms_l))
     counts = _fluid_counts(f)
     bytes_per_launch = counts[L] * 2 * 19 * BYTES_PER_VALUE[precision]
@@ -163,8 +163,11 @@ def _roofline(f, lev, precision, peaks, peak_kind):
     achieved = bytes_per_launch / avg_s / 1e9
     peak = float(peaks["hbm_gbs"])
     traffic = _ncu_traffic(precision)
+    total = ms_l.sum() + ems_l.sum()
+    share = ms_l / total
     per_level = [{"level": i, "launches": int(cnt_l[i]), "ms_total": round(float(ms_l[i]), 4),
-                  "share": round(float(share[i]), 4),
+                  "share": round(float(share[i]), 4), "explode_launches": int(ecnt_l[i]),
+                  "explode_ms_total": round(float(ems_l[i]), 4),
                   "GBps_algorithmic": round(counts[i] * 2 * 19 * BYTES_PER_VALUE[precision] / (ms_l[i] / cnt_l[i] / 1e3) / 1e9, 1)
                   if cnt_l[i] else None} for i in range(f.nlev)]
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -326,7 +329,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    lev = f.timing_end()
+    lev = f.timing_end(explode=True)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

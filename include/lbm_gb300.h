@@ -154,9 +154,10 @@ lbm_status lbm_set_level_params_explicit(lbm_forest* f, const double* lambda_e,
 lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho, const double* u,
                                 int32_t on_device);
 
-/* Advances n_steps coarse time steps: Alg. 1 with the finer level's explosion reads, same-level
- * exchange and coalescence fused into each level's stream-collide kernel (Alg. 2).  The whole
- * coarse step is one CUDA graph, replayed per step on the forest's stream; asynchronous. */
+/* Advances n_steps coarse time steps: Alg. 1 with same-level exchange, boundary treatment and
+ * coalescence fused into each level's stream-collide kernel (Alg. 2), and one explosion kernel
+ * per visit of a finer level.  The whole coarse step is one CUDA graph, replayed per step on
+ * the forest's stream; asynchronous. */
 lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps);
 
 /* Macroscopic fields (Eq. fvelocity; the velocity adds a_L/2 as in Sec. 2.1) of the current
@@ -179,10 +180,12 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
 /* ---- measurement -------------------------------------------------------------------------
  * lbm_timing_begin(f, max_steps) makes the next lbm_step_coarse calls (at most max_steps
  * coarse steps in total) record CUDA events around every kernel of the captured graph, on the
- * forest's stream.  lbm_timing_end synchronises and returns, per level, the summed kernel
- * time in ms and the number of launches (arrays of length n_levels), then stops timing. */
+ * forest's stream.  lbm_timing_end synchronises and returns, per level, the summed time in ms
+ * and the number of launches of the stream-collide kernels and of the explosion kernels
+ * (arrays of length n_levels; any may be NULL), then stops timing. */
 lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);
-lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level);
+lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level,
+                          double* ms_explode_per_level, int64_t* launches_explode_per_level);
 
 /* Thread mapping of the stream-collide kernel (results do not depend on it): each thread walks
  * 2^cells_per_thread_log2 cells (<= B) of one z-column of a block, and the kernel variant is

@@ -2,9 +2,10 @@
 //
 // The level schedule restates Alg. 1 with every collision fused into the preceding
 // stream (the kernels store post-collision states, Alg. 2's StreamCollide applied on all
-// levels).  Per coarse step, with F_L(s) the fused kernel of level L in its sub-step s:
-//     S(0) = [S(1)] F_0(1)          S(L) = [S(L+1)] F_L(1) [S(L+1)] F_L(2)   (L >= 1)
-// F_L(1) carries explosion (reads of the coarse post-collision parent for ghost layers),
+// levels).  Per coarse step, with F_L(s) the fused kernel of level L in its sub-step s and
+// E_L the explosion into level L's ghost layers:
+//     S(0) = [S(1)] F_0(1)      S(L) = E_L [S(L+1)] F_L(1) [S(L+1)] F_L(2)   (L >= 1)
+// E_L copies the coarse post-collision state into ghost layers 1-4 (Eq. ctof); F_L(1) carries
 // stream, coalescence (reads of the finer ghost layers) and the second collision of Alg. 1;
 // F_L(2) carries the second stream and the first collision of the next visit.  Levels >= 1
 // flip their two-grid parity an even number of times per coarse step, level 0 once; the
@@ -47,6 +48,7 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
 
 struct Launch {
     int level, substep, grid;
+    int type;   // 0: stream-collide F_L(substep), 1: explosion E_L
 };
 
 struct DevBuf {
@@ -56,6 +58,8 @@ struct DevBuf {
     uint8_t* kind = nullptr;
     uint32_t* link = nullptr;
     uint32_t* glink = nullptr;
+    uint32_t* colsolid = nullptr;
+    int32_t* ecells = nullptr;
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -115,7 +119,6 @@ struct lbm_forest {
     int64_t updates = 0;
     int lzc = 3;        // log2 of the cells per thread along z in the owned part of the step kernel
     int minb = 3;       // CTAs per SM of the step-kernel variant
-    bool explode_pending = true;   // ghost layers must be exploded from the coarser level
 };
 
 namespace {
@@ -169,7 +172,11 @@ void build_schedule(lbm_forest* f) {
         const HostLevel& V = f->plan.lv[L];
         const int64_t units = int64_t(V.nown) * B * B * (B >> f->lzc);
         int grid = int((units + 255) / 256) + int((V.gcells.size() + 255) / 256);
-        f->sched.push_back({L, s, grid});
+        f->sched.push_back({L, s, grid, 0});
+    };
+    auto explode = [&](int L) {
+        const HostLevel& V = f->plan.lv[L];
+        f->sched.push_back({L, 0, int((V.ecells.size() + 255) / 256), 1});
     };
     std::function<void(int)> rec = [&](int L) {
         if (L == 0) {
@@ -177,6 +184,7 @@ void build_schedule(lbm_forest* f) {
             push(0, 1);
             return;
         }
+        explode(L);
         if (L + 1 < n) rec(L + 1);
         push(L, 1);
         if (L + 1 < n) rec(L + 1);
@@ -199,6 +207,10 @@ lbm_status capture(lbm_forest* f, int timed, int parity) {
     for (size_t k = 0; k < f->sched.size(); k++) {
         const Launch& l = f->sched[k];
         if (timed) CU(cudaEventRecordWithFlags(evs[k], f->cap, cudaEventRecordExternal));
+        if (l.type == 1) {
+            f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], f->plan.LB, f->cap);
+            continue;
+        }
         StepArgs a = make_args(f, l, cur);
         f->L->step(a, f->plan.d.collision, l.grid, f->cap);
         cur[l.level] ^= 1;
@@ -231,16 +243,6 @@ lbm_status capture(lbm_forest* f, int timed, int parity) {
         for (cudaGraphNode_t nd : f->ev_nodes[parity])
             if (!nd) return fail(LBM_ECUDA, "timing event node missing from the captured graph");
     }
-    return LBM_OK;
-}
-
-// Fills ghost layers 1-4 of every level from its coarser level (Eq. ctof); the step kernels keep
-// them up to date afterwards by pushing the explosion from the coarse side.
-lbm_status explode_all(lbm_forest* f) {
-    for (int L = 1; L < f->plan.nlev; L++)
-        f->L->explode(f->dl[L], f->dl[L - 1], f->cur[L], f->cur[L - 1], f->plan.LB, f->stream);
-    CU(cudaGetLastError());
-    f->explode_pending = false;
     return LBM_OK;
 }
 
@@ -327,7 +329,7 @@ lbm_status lbm_plan_counts(const lbm_plan* p, int32_t level, int64_t counts[4]) 
     const HostLevel& V = p->p.lv[level];
     counts[0] = V.nown;
     counts[1] = V.nfluid;
-    counts[2] = int64_t(V.gcells.size());
+    counts[2] = V.nghost12;
     counts[3] = V.nghost;
     return LBM_OK;
 }
@@ -354,6 +356,8 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.kind);
         cudaFree(b.link);
         cudaFree(b.glink);
+        cudaFree(b.colsolid);
+        cudaFree(b.ecells);
     }
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
@@ -403,7 +407,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         lbm_status s;
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
-            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)))
+            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)) ||
+            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.ecells, V.ecells)))
             return bail(s);
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -417,6 +422,9 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.gcells = b.gcells;
         g.link = b.link;
         g.glink = b.glink;
+        g.colsolid = b.colsolid;
+        g.ecells = b.ecells;
+        g.necells = int(V.ecells.size());
         g.nown = V.nown;
         g.nbricks = V.nbricks();
         g.ngcells = int(V.gcells.size());
@@ -529,7 +537,6 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
         }
         CU(cudaGetLastError());
         f->init_mask = (1u << P.nlev) - 1;
-        f->explode_pending = true;
         return LBM_OK;
     }
     lbm_status s = check_level(f, level);
@@ -550,7 +557,6 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
-    f->explode_pending = true;
     return LBM_OK;
 }
 
@@ -559,10 +565,6 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
     if (n_steps < 0) return fail(LBM_EINVAL, "negative step count");
     if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
         return fail(LBM_EINVAL, "set the level parameters and initialise every level before stepping");
-    if (f->explode_pending) {
-        lbm_status s = explode_all(f);
-        if (s) return s;
-    }
     for (int i = 0; i < n_steps; i++) {
         const int p = f->cur[0];
         const int timed = f->timing && f->tused < f->tmax ? 1 : 0;
@@ -641,7 +643,6 @@ lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
-    f->explode_pending = true;
     return LBM_OK;
 }
 
@@ -696,24 +697,28 @@ lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps) {
     return LBM_OK;
 }
 
-lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level) {
+lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level, double* ms_explode,
+                          int64_t* launches_explode) {
     if (!f) return fail(LBM_EINVAL, "forest is NULL");
     CU(cudaStreamSynchronize(f->stream));
     const int n = f->plan.nlev;
-    std::vector<double> ms(n, 0.0);
-    std::vector<int64_t> cnt(n, 0);
+    std::vector<double> ms(2 * n, 0.0);
+    std::vector<int64_t> cnt(2 * n, 0);
     const size_t ne = f->sched.size() + 1;
     for (int r = 0; r < f->tused; r++)
         for (size_t k = 0; k + 1 < ne; k++) {
-            if (f->sched[k].grid <= 0) continue;
+            const Launch& l = f->sched[k];
+            if (l.grid <= 0) continue;
             float t = 0.f;
             CU(cudaEventElapsedTime(&t, f->tev[r * ne + k], f->tev[r * ne + k + 1]));
-            ms[f->sched[k].level] += t;
-            cnt[f->sched[k].level] += 1;
+            ms[2 * l.level + l.type] += t;
+            cnt[2 * l.level + l.type] += 1;
         }
     for (int L = 0; L < n; L++) {
-        if (ms_per_level) ms_per_level[L] = ms[L];
-        if (launches_per_level) launches_per_level[L] = cnt[L];
+        if (ms_per_level) ms_per_level[L] = ms[2 * L];
+        if (launches_per_level) launches_per_level[L] = cnt[2 * L];
+        if (ms_explode) ms_explode[L] = ms[2 * L + 1];
+        if (launches_explode) launches_explode[L] = cnt[2 * L + 1];
     }
     free_timing(f);
     return LBM_OK;

@@ -263,7 +263,7 @@ struct Builder {
                         else ck = dmin <= 2 ? CK_GHOST : (dmin <= 4 ? CK_G34 : CK_FAR);
                         int c = (z * B + y) * B + x;
                         cells[c] = ck;
-                        if (ck == CK_GHOST) V.gcells.push_back(int32_t(size_t(k) * B3 + c));
+                        if (ck == CK_GHOST) V.nghost12++;
                     }
             // a ghost brick without obstacle cells: every source in it is a stored value
             bool pure = true;
@@ -303,10 +303,9 @@ struct Builder {
         return m;
     }
 
-    // Owned cells: link bits, bit 31 for non-fluid cells, and the explosion code in bits 29-30:
-    // 1 when the cell's 8 children on level L+1 are fluid ghost cells of layers 1-2, 2 when they
-    // are of layers 3-4 (Eq. ctof pushes the post-collision value into them).  Ghost work list:
-    // link bits only.
+    // Owned cells: link bits and bit 31 for non-fluid cells; per owned column the bitmap of its
+    // non-fluid cells.  Ghost bricks: the stream and explosion work lists, in whole 32-byte groups
+    // of a row (group = 32 bytes / PDF size cells) so that every write covers full sectors.
     void links(int L) {
         HostLevel& V = p.lv[L];
         const int B = p.B, B3 = B * B * B;
@@ -319,31 +318,42 @@ struct Builder {
             if (plain) V.kind[k] |= BK_PLAIN;
         }
         V.link.assign(size_t(V.nown) * B3, 0u);
-        const HostLevel* F = L + 1 < p.nlev ? &p.lv[L + 1] : nullptr;
+        V.colsolid.assign(size_t(V.nown) * B * B, 0u);
         for (int k = 0; k < V.nown; k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
                     for (int x = 0; x < B; x++) {
                         const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
                         uint32_t m = link_bits(V, k, x, y, z, true);
-                        if (V.cell[c] != CK_FLUID) m |= 1u << 31;
-                        if (F && V.cell[c] == CK_FLUID) {
-                            const int oct = ((2 * x) / B) | (((2 * y) / B) << 1) | (((2 * z) / B) << 2);
-                            const int32_t cb = V.child[size_t(k) * 8 + oct];
-                            if (cb >= 0) {
-                                const int cx = (2 * x) % B, cy = (2 * y) % B, cz = (2 * z) % B;
-                                const uint8_t ck = F->cell[size_t(cb) * B3 + (size_t(cz) * B + cy) * B + cx];
-                                if (ck == CK_GHOST) m |= 1u << 29;
-                                else if (ck == CK_G34) m |= 2u << 29;
-                            }
+                        if (V.cell[c] != CK_FLUID) {
+                            m |= 1u << 31;
+                            V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
                         }
                         V.link[c] = m;
                     }
-        V.glink.resize(V.gcells.size());
-        for (size_t i = 0; i < V.gcells.size(); i++) {
-            const int c = V.gcells[i], k = c / B3, r = c % B3;
-            V.glink[i] = link_bits(V, k, r % B, (r / B) % B, r / (B * B), false);
-        }
+        const int esize = p.d.precision == LBM_FP64 ? 8 : (p.d.precision == LBM_FP32S ? 4 : 2);
+        const int G = std::min(32 / esize, B);
+        for (int k = V.nown; k < V.nbricks(); k++)
+            for (int z = 0; z < B; z++)
+                for (int y = 0; y < B; y++)
+                    for (int x0 = 0; x0 < B; x0 += G) {
+                        const size_t row = size_t(k) * B3 + (size_t(z) * B + y) * B;
+                        bool g12 = false, g14 = false;
+                        for (int x = x0; x < x0 + G; x++) {
+                            const uint8_t ck = V.cell[row + x];
+                            g12 = g12 || ck == CK_GHOST;
+                            g14 = g14 || ck == CK_GHOST || ck == CK_G34;
+                        }
+                        for (int x = x0; x < x0 + G && g12; x++) {
+                            const int c = int(row + x);
+                            V.gcells.push_back(c);
+                            V.glink.push_back(V.cell[c] == CK_GHOST ? link_bits(V, k, x, y, z, false) : (1u << 30));
+                        }
+                        for (int x = x0; x < x0 + G && g14; x++) {
+                            const int c = int(row + x);
+                            V.ecells.push_back(V.cell[c] == CK_G34 ? int32_t(uint32_t(c) | (1u << 31)) : c);
+                        }
+                    }
     }
 
     void children(int L) {

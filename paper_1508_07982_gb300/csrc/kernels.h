@@ -29,7 +29,10 @@ struct DevLevel {
     const int32_t* gcells;
     const uint32_t* link; // [nown * B^3] per owned cell: bit q set = link q needs the general pull;
                           // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
-    const uint32_t* glink;  // [ngcells] link bits of the ghost work list
+    const uint32_t* glink;  // [ngcells] link bits of the ghost work list; bit 30 = copy only
+    const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
+    const int32_t* ecells;     // explosion targets; bit 31 = ghost layers 3-4
+    int necells;
     int nown, nbricks, ngcells;
     int64_t ncells;
     int N[3];
@@ -50,7 +53,7 @@ struct StepArgs {
 
 // Bits of the per-cell link mask.
 constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
-constexpr uint32_t LINK_EXPLODE = 3u << 29;
+constexpr uint32_t LINK_COPY = 1u << 30;
 constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18
 
 // Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).

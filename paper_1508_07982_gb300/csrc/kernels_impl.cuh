@@ -52,9 +52,8 @@ struct LaunchImpl {
         reduce_level_kernel<T><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, w, partial);
     }
     static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int LB, cudaStream_t s) {
-        const int64_t n = lv.ncells - (int64_t(lv.nown) << (3 * LB));
-        if (n <= 0) return;
-        explode_level_kernel<T><<<int((n + 255) / 256), 256, 0, s>>>(lv, co, cur, cur_c, LB);
+        if (lv.necells <= 0) return;
+        explode_kernel<T><<<(lv.necells + 255) / 256, 256, 0, s>>>(lv, co, cur, cur_c, LB);
     }
     static const Launchers& get() {
         static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode};

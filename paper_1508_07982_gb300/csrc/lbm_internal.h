@@ -41,10 +41,15 @@ struct HostLevel {
     std::vector<int32_t> child;    // [nown][8] ghost brick of L+1 under each octant, or -1
     std::vector<uint8_t> kind;     // [nbricks] BK_* bits
     std::vector<uint8_t> cell;     // [nbricks * B^3] CK_* per cell
-    std::vector<int32_t> gcells;   // cell indices of CK_GHOST cells (the ghost work list)
+    std::vector<int32_t> gcells;   // ghost stream work list: every cell of each 32-byte group of a
+                                   // row that holds a ghost-layer-1/2 fluid cell
+    std::vector<uint32_t> glink;   // [gcells] link bits; bit 30 = not a layer-1/2 fluid cell (copy)
+    std::vector<int32_t> ecells;   // explosion targets: every cell of each 32-byte group of a row that
+                                   // holds a fluid cell of ghost layers 1-4; bit 31 = layers 3-4
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
-                                   // same-level load; bits 29-30 = explosion code; bit 31 = not fluid
-    std::vector<uint32_t> glink;   // [gcells] the same link bits for the ghost work list
+                                   // same-level load; bit 31 = not fluid
+    std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
+    int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }
 };

@@ -206,39 +206,13 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     return qnan<C>();
 }
 
-// Explosion (Eq. ctof) pushed from the coarse side: the post-collision value v of owned cell
-// (x, y, z) of brick `brick` goes to its 8 children on the next finer level.  Children in ghost
-// layers 1-2 (code 1) are written to the finer level's current grid, which its next first
-// sub-step reads; children in layers 3-4 (code 2), never streamed, are written to both grids.
-template <typename T, typename C, int LB>
-__device__ __forceinline__ void explode_children(const StepArgs& a, int brick, int x, int y, int z, int code,
-                                                 const C (&v)[19]) {
-    constexpr int B = 1 << LB, M = B - 1, B3s = 3 * LB;
-    const int oct = ((2 * x) >> LB) | (((2 * y) >> LB) << 1) | (((2 * z) >> LB) << 2);
-    const int cb = __ldg(a.lv.child + brick * 8 + oct);
-    if (cb < 0) return;
-    const int cx = (2 * x) & M, cy = (2 * y) & M, cz = (2 * z) & M;
-    const int64_t base = (int64_t(cb) << B3s) + (cz << (2 * LB)) + (cy << LB) + cx;
-    const int64_t nf = a.fi.ncells;
-    T* g0 = static_cast<T*>(a.fi.f[a.cur_f]);
-    T* g1 = static_cast<T*>(a.fi.f[a.cur_f ^ 1]);
-    for (int j = 0; j < 8; j++) {
-        const int64_t idx = base + ((j >> 2) << (2 * LB)) + (((j >> 1) & 1) << LB) + (j & 1);
-#pragma unroll
-        for (int q = 0; q < 19; q++) {
-            Store<T>::st(g0 + int64_t(q) * nf + idx, v[q]);
-            if (code == 2) Store<T>::st(g1 + int64_t(q) * nf + idx, v[q]);
-        }
-    }
-}
-
 // One sub-step of one level (Alg. 2 StreamCollide generalised to every level): pull stream with
-// boundary treatment and coalescence, collide owned cells, push the explosion into the finer
-// level's ghost layers; ghost layers 1-2 of this level are streamed only.  Owned cells: each
-// thread walks 2^lzc cells of one (x, y) column of a brick; the source offsets of a cell inside
-// the brick are computed once per column, and a per-cell link mask (read where the column needs
-// it) routes the few links that are not plain loads to pull_general.  CTAs after the owned part
-// cover the ghost work list.
+// boundary treatment and coalescence, then collide owned cells; ghost layers 1-2 are streamed
+// only (their sources were filled by explode_kernel).  Owned cells: each thread walks 2^lzc cells
+// of one (x, y) column of a brick; the source offsets of a cell inside the brick are computed once
+// per column, obstacle cells are skipped by a per-column bitmap, and a per-cell link mask (read
+// where the brick needs it) routes the few links that are not plain loads to pull_general.  CTAs
+// after the owned part cover the ghost work list, in whole 32-byte groups.
 template <typename T, typename C, int COLL, int LB, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
@@ -274,6 +248,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int nb = (ox | oy) ? __ldg(nbr + 13 + ox + 3 * oy) : brick;
             off[q] = (max(nb, 0) << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s);
         }
+        const uint32_t solid = need_mask ? __ldg(a.lv.colsolid + (brick << B2s) + col) : 0u;
         const LevelParams* P = a.params;
         const C le = Par<C>::le(P), lo = Par<C>::lo(P);
         const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
@@ -282,6 +257,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int z = z0 + k;
             const int zoff = z << B2s;
             const int cidx = (brick << B3s) + zoff + (y << LB) + x;
+            if ((solid >> z) & 1u) continue;
             // The loads do not wait for the link mask: every address below lies inside the level's
             // grid, and the links the mask marks are replaced afterwards.  On the brick's z faces
             // the links that leave the brick read the z-neighbour brick (z is uniform in a warp).
@@ -304,7 +280,6 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
                     v[q] = C(Store<T>::ld(p + s));
                 }
             }
-            if (m & LINK_NOT_FLUID) continue;
             const uint32_t mq = m & LINK_ALL;
             if (mq) {
                 for (int q = 1; q < 19; q++)
@@ -322,7 +297,6 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
                     p += n;
                 }
             }
-            if (m & LINK_EXPLODE) explode_children<T, C, LB>(a, brick, x, y, z, int((m & LINK_EXPLODE) >> 29), v);
         }
         return;
     }
@@ -349,7 +323,16 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             v[q] = C(Store<T>::ld(p + sidx));
         }
     }
-    const uint32_t mq = __ldg(a.lv.glink + i);
+    const uint32_t gm = __ldg(a.lv.glink + i);
+    if (gm & LINK_COPY) {
+        // not a layer-1/2 fluid cell: keep the stored value (layers 3-4 hold the exploded value)
+        const T* p = src + c;
+        T* d = dst + c;
+#pragma unroll
+        for (int q = 0; q < 19; q++) d[int64_t(q) * n] = p[int64_t(q) * n];
+        return;
+    }
+    const uint32_t mq = gm & LINK_ALL;
     if (mq) {
         for (int q = 1; q < 19; q++)
             if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
@@ -365,30 +348,33 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     }
 }
 
-// Explosion of a whole level from its coarser level (Eq. ctof), used after the state is set from
-// outside (initial equilibrium, checkpoint): every fluid cell of ghost layers 1-4 takes its coarse
-// parent's value, in the current grid, and layers 3-4 in both grids.
+// Explosion (Eq. ctof): at the start of every visit of a finer level, each cell of its
+// explosion list takes all 19 values of its coarse parent's post-collision state, in the finer
+// level's current grid; cells of ghost layers 3-4 (never streamed) also in the other grid, which
+// the second sub-step reads.  The list holds whole 32-byte groups of a row; the extra cells are
+// never read.
 template <typename T>
-__global__ void explode_level_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c, int LB) {
-    const int B3s = 3 * LB, M = (1 << LB) - 1;
-    const int64_t first = int64_t(lv.nown) << B3s;
-    const int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= lv.ncells) return;
-    const uint8_t ck = lv.cell[i];
-    if (ck != CK_GHOST && ck != CK_G34) return;
-    const int g = int(i >> B3s), local = int(i & ((int64_t(1) << B3s) - 1));
+__global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c, int LB) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= lv.necells) return;
+    const uint32_t e = uint32_t(__ldg(lv.ecells + i));
+    const int c = int(e & 0x7FFFFFFFu);
+    const int B3s = 3 * LB, M = (1 << LB) - 1, B = 1 << LB;
+    const int g = c >> B3s, local = c & ((1 << B3s) - 1);
     const int x = local & M, y = (local >> LB) & M, z = local >> (2 * LB);
-    const int pk = lv.parent[g];
-    const int pb = pk >> 3, oct = pk & 7, B = 1 << LB;
+    const int pk = __ldg(lv.parent + g);
+    const int pb = pk >> 3, oct = pk & 7;
     const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1, pz = ((oct >> 2) * B + z) >> 1;
-    const int64_t pidx = (int64_t(pb) << B3s) + (pz << (2 * LB)) + (py << LB) + px;
-    const T* cf = static_cast<const T*>(co.f[cur_c]);
-    T* f0 = static_cast<T*>(lv.f[cur]);
-    T* f1 = static_cast<T*>(lv.f[cur ^ 1]);
+    const int pidx = (pb << B3s) + (pz << (2 * LB)) + (py << LB) + px;
+    const T* cf = static_cast<const T*>(co.f[cur_c]) + pidx;
+    T* f0 = static_cast<T*>(lv.f[cur]) + c;
+    T* f1 = static_cast<T*>(lv.f[cur ^ 1]) + c;
+    const bool both = e >> 31;
+#pragma unroll
     for (int q = 0; q < 19; q++) {
-        const T v = cf[q * co.ncells + pidx];
-        f0[q * lv.ncells + i] = v;
-        if (ck == CK_G34) f1[q * lv.ncells + i] = v;
+        const T v = cf[int64_t(q) * co.ncells];
+        f0[int64_t(q) * lv.ncells] = v;
+        if (both) f1[int64_t(q) * lv.ncells] = v;
     }
 }
 

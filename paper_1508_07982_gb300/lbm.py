@@ -94,7 +94,7 @@ def library():
             "lbm_set_pdfs": [P, ctypes.c_int32, P, ctypes.c_int32],
             "lbm_reduce_mass_momentum": [P, dp],
             "lbm_timing_begin": [P, ctypes.c_int32],
-            "lbm_timing_end": [P, dp, i64p],
+            "lbm_timing_end": [P, dp, i64p, dp, i64p],
             "lbm_launches_per_coarse_step": [P, i32p],
             "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_get_kernel_config": [P, i32p, i32p],
@@ -350,8 +350,13 @@ class Forest:
     def timing_begin(self, max_steps):
         _check(library().lbm_timing_begin(self.h, max_steps))
 
-    def timing_end(self):
+    def timing_end(self, explode=False):
+        """Per level: (ms, launches) of the stream-collide kernels; with explode=True also the
+        explosion kernels' (ms, launches)."""
         ms = np.zeros(self.nlev)
         cnt = np.zeros(self.nlev, np.int64)
-        _check(library().lbm_timing_end(self.h, _dp(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
-        return ms, cnt
+        ems = np.zeros(self.nlev)
+        ecnt = np.zeros(self.nlev, np.int64)
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        _check(library().lbm_timing_end(self.h, _dp(ms), cnt.ctypes.data_as(i64), _dp(ems), ecnt.ctypes.data_as(i64)))
+        return (ms, cnt, ems, ecnt) if explode else (ms, cnt)

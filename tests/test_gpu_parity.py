@@ -209,10 +209,11 @@ def test_timing_api_reports_every_launch(lbm):
     f.step_coarse(2)
     f.timing_begin(5)
     f.step_coarse(5)
-    ms, cnt = f.timing_end()
-    assert cnt.tolist() == [5, 10]
-    assert (ms > 0).all()
-    assert f.launches_per_coarse_step() == 3
+    ms, cnt, ems, ecnt = f.timing_end(explode=True)
+    assert cnt.tolist() == [5, 10]           # level 1 takes two sub-steps per coarse step
+    assert ecnt.tolist() == [0, 5]           # one explosion per visit of level 1
+    assert (ms > 0).all() and ems[1] > 0
+    assert f.launches_per_coarse_step() == 4
 
 
 def test_thread_mapping_does_not_change_results(lbm):
