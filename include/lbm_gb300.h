@@ -197,6 +197,32 @@ lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_
 /* Number of kernel launches one coarse step issues (the nodes of the captured graph). */
 lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n);
 
+/* ---- totals without allocation ------------------------------------------------------------
+ * The paper has no counterpart: this entry point serves callers that cannot allocate device
+ * memory when they need mass and momentum totals (code running during CUDA stream capture,
+ * where cudaMalloc is not allowed; runtimes that own all device memory through their own pool;
+ * hosts that forbid dynamic allocation after start-up).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its per-CTA partial sums live in one fixed device array of
+ * (LBM_NOALLOC_MAX_CELLS / LBM_NOALLOC_CELLS_PER_CTA) x 4 doubles = 512 KiB, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *   pdfs      device pointer, [19][n_cells] in the storage layout of `precision` (LBM_FP64: f;
+ *             LBM_FP32S / LBM_FP16S: f - w rho0), e.g. the output of lbm_get_pdfs
+ *   n_cells   0 .. LBM_NOALLOC_MAX_CELLS; larger counts return LBM_EINVAL without launching
+ *   rho0      reference density (adds back the shift of the shifted layouts)
+ *   out       device pointer to 4 doubles: {sum rho, sum j_x, sum j_y, sum j_z} with
+ *             j = sum_a e_a f_a; cells whose 19 values are not all finite (obstacles) are skipped
+ *   stream    cudaStream_t; the call is asynchronous
+ * The first call on each device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress); make that first call before capturing any stream on that device.
+ * All calls share the array and it keeps the last call's partial sums; every call writes each
+ * slot it reads, so nothing has to be cleared, but calls that overlap on the GPU (other streams
+ * or threads without ordering between them) race on it and return wrong totals. */
+#define LBM_NOALLOC_CELLS_PER_CTA 4096
+#define LBM_NOALLOC_MAX_CELLS (16384 * 4096)
+lbm_status lbm_mass_momentum_noalloc(const void* pdfs, int32_t precision, int64_t n_cells, double rho0,
+                                     double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,8 @@ size_t elem_size(int precision) { return precision == LBM_FP64 ? 8 : (precision 
 
 }  // namespace
 
+void lbm::set_last_error(const char* msg) { g_err = msg; }
+
 struct lbm_forest {
     Plan plan;
     cudaStream_t stream = nullptr;

@@ -67,6 +67,8 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
                 std::string& err);
 double scale_rate(double w0, int L);
 double lambda_odd(double le, double magic);
+// Sets the thread-local text that lbm_last_error returns.
+void set_last_error(const char* msg);
 
 }  // namespace lbm
 

@@ -28,7 +28,9 @@ EXPORTS = [
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
     "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
+    "lbm_mass_momentum_noalloc",
 ]
+NOALLOC_MAX_CELLS = 16384 * 4096
 
 
 class LBMError(RuntimeError):
@@ -98,6 +100,7 @@ def library():
             "lbm_launches_per_coarse_step": [P, i32p],
             "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_get_kernel_config": [P, i32p, i32p],
+            "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -173,6 +176,18 @@ def make_desc(case, precision="fp64"):
         for k in range(8):
             d.regions[i][k] = vals[k]
     return d
+
+
+def lbm_mass_momentum_noalloc(pdfs, precision, n_cells, rho0, out, stream=None):
+    """Totals of a device PDF array without any allocation (see include/lbm_gb300.h).  pdfs and
+    out are device tensors (or raw device addresses); out receives 4 doubles."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    p = pdfs if isinstance(pdfs, int) else pdfs.data_ptr()
+    o = out if isinstance(out, int) else out.data_ptr()
+    _check(library().lbm_mass_momentum_noalloc(ctypes.c_void_p(p), PRECISION[precision], n_cells, rho0,
+                                                ctypes.c_void_p(o), ctypes.c_void_p(stream)))
 
 
 class Plan:
