@@ -189,7 +189,7 @@ lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches
 
 /* Thread mapping of the stream-collide kernel (results do not depend on it): each thread walks
  * 2^cells_per_thread_log2 cells (<= B) of one z-column of a block, and the kernel variant is
- * compiled for ctas_per_sm (2 or 3) resident 256-thread CTAs per SM.  Synchronises the stream
+ * compiled for ctas_per_sm (2, 3 or 4) resident 256-thread CTAs per SM.  Synchronises the stream
  * and drops the captured graphs; the next lbm_step_coarse captures them again. */
 lbm_status lbm_set_kernel_config(lbm_forest* f, int32_t cells_per_thread_log2, int32_t ctas_per_sm);
 lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm);

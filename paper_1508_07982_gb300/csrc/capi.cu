@@ -60,6 +60,7 @@ struct DevBuf {
     uint32_t* glink = nullptr;
     uint32_t* colsolid = nullptr;
     int32_t* ecells = nullptr;
+    int32_t* eparent = nullptr;
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -360,6 +361,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.glink);
         cudaFree(b.colsolid);
         cudaFree(b.ecells);
+        cudaFree(b.eparent);
     }
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
@@ -410,7 +412,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
             (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)) ||
-            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.ecells, V.ecells)))
+            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.ecells, V.ecells)) ||
+            (s = upload(&b.eparent, V.eparent)))
             return bail(s);
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -426,6 +429,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.glink = b.glink;
         g.colsolid = b.colsolid;
         g.ecells = b.ecells;
+        g.eparent = b.eparent;
         g.necells = int(V.ecells.size());
         g.nown = V.nown;
         g.nbricks = V.nbricks();
@@ -671,7 +675,7 @@ lbm_status lbm_set_kernel_config(lbm_forest* f, int32_t cells_per_thread_log2, i
     if (!f) return fail(LBM_EINVAL, "forest is NULL");
     if (cells_per_thread_log2 < 0 || cells_per_thread_log2 > f->plan.LB)
         return fail(LBM_EINVAL, "cells per thread must be 2^k with 2^k <= B");
-    if (ctas_per_sm != 2 && ctas_per_sm != 3) return fail(LBM_EINVAL, "ctas_per_sm must be 2 or 3");
+    if (ctas_per_sm < 2 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 2, 3 or 4");
     CU(cudaStreamSynchronize(f->stream));
     free_graphs(f);
     f->lzc = cells_per_thread_log2;

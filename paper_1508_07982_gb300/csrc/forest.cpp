@@ -303,6 +303,23 @@ struct Builder {
         return m;
     }
 
+    // True when every link in m pulls from an obstacle cell of this level that no coalescence
+    // replaces, so the pull is the cell's own opposite value (no-slip bounce-back, Sec. 2.2).
+    bool bounce_only(const HostLevel& V, int k, int x, int y, int z, uint32_t m) const {
+        const int B = p.B, B3 = B * B * B, M = B - 1;
+        const int32_t* nbr = &V.nbr[size_t(k) * 27];
+        if (V.kind[k] & BK_TOUCH_FINER) return false;
+        for (int q = 1; q < Q; q++) {
+            if (!((m >> q) & 1u)) continue;
+            int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
+            for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
+            int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
+            if (nb < 0) return false;
+            if (V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] != CK_SOLID) return false;
+        }
+        return true;
+    }
+
     // Owned cells: link bits and bit 31 for non-fluid cells; per owned column the bitmap of its
     // non-fluid cells.  Ghost bricks: the stream and explosion work lists, in whole 32-byte groups
     // of a row (group = 32 bytes / PDF size cells) so that every write covers full sectors.
@@ -325,6 +342,7 @@ struct Builder {
                     for (int x = 0; x < B; x++) {
                         const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
                         uint32_t m = link_bits(V, k, x, y, z, true);
+                        if (m && bounce_only(V, k, x, y, z, m)) m |= 1u << 29;
                         if (V.cell[c] != CK_FLUID) {
                             m |= 1u << 31;
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
@@ -352,6 +370,10 @@ struct Builder {
                         for (int x = x0; x < x0 + G && g14; x++) {
                             const int c = int(row + x);
                             V.ecells.push_back(V.cell[c] == CK_G34 ? int32_t(uint32_t(c) | (1u << 31)) : c);
+                            const int pk = V.parent[k], pb = pk >> 3, oct = pk & 7;
+                            const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1;
+                            const int pz = ((oct >> 2) * B + z) >> 1;
+                            V.eparent.push_back(int32_t(size_t(pb) * B3 + (size_t(pz) * B + py) * B + px));
                         }
                     }
     }

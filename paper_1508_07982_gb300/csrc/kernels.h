@@ -32,6 +32,7 @@ struct DevLevel {
     const uint32_t* glink;  // [ngcells] link bits of the ghost work list; bit 30 = copy only
     const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
     const int32_t* ecells;     // explosion targets; bit 31 = ghost layers 3-4
+    const int32_t* eparent;    // coarse parent cell of each explosion target
     int necells;
     int nown, nbricks, ngcells;
     int64_t ncells;
@@ -44,7 +45,7 @@ struct StepArgs {
     int substep;          // 1: ghost layers hold exploded values; 2: they hold sub-step-1 values
     int LB;
     int lzc;              // log2 of the cells each thread walks along z
-    int minb;             // CTAs per SM the kernel variant is compiled for (2 or 3)
+    int minb;             // CTAs per SM the kernel variant is compiled for (2, 3 or 4)
     int per;              // bit a set: axis a periodic
     const LevelParams* params;
     const double* wall;   // [6][19] 6 w_a rho0 (e_a . u_w) per face
@@ -54,6 +55,7 @@ struct StepArgs {
 // Bits of the per-cell link mask.
 constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
 constexpr uint32_t LINK_COPY = 1u << 30;
+constexpr uint32_t LINK_BOUNCE_ONLY = 1u << 29;
 constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18
 
 // Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).

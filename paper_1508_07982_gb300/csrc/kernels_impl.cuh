@@ -15,6 +15,7 @@ struct LaunchImpl {
     template <int COLL>
     static void step_b(const StepArgs& a, int grid, cudaStream_t s) {
         if (a.minb == 2) step_m<COLL, 2>(a, grid, s);
+        else if (a.minb == 4) step_m<COLL, 4>(a, grid, s);
         else step_m<COLL, 3>(a, grid, s);
     }
     static void step(const StepArgs& a, int collision, int grid, cudaStream_t s) {
@@ -53,7 +54,8 @@ struct LaunchImpl {
     }
     static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int LB, cudaStream_t s) {
         if (lv.necells <= 0) return;
-        explode_kernel<T><<<(lv.necells + 255) / 256, 256, 0, s>>>(lv, co, cur, cur_c, LB);
+        (void)LB;
+        explode_kernel<T><<<dim3((lv.necells + 255) / 256, 19), 256, 0, s>>>(lv, co, cur, cur_c);
     }
     static const Launchers& get() {
         static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode};

@@ -46,8 +46,10 @@ struct HostLevel {
     std::vector<uint32_t> glink;   // [gcells] link bits; bit 30 = not a layer-1/2 fluid cell (copy)
     std::vector<int32_t> ecells;   // explosion targets: every cell of each 32-byte group of a row that
                                    // holds a fluid cell of ghost layers 1-4; bit 31 = layers 3-4
+    std::vector<int32_t> eparent;  // [ecells] the coarse parent cell of each target on level L-1
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
-                                   // same-level load; bit 31 = not fluid
+                                   // same-level load; bit 29 = every such link is a no-slip
+                                   // bounce-back from an obstacle cell; bit 31 = not fluid
     std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
     int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells

@@ -281,7 +281,13 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
                 }
             }
             const uint32_t mq = m & LINK_ALL;
-            if (mq) {
+            if (m & LINK_BOUNCE_ONLY) {
+                // every marked link bounces back from an obstacle: the cell's own opposite value
+                const T* p = src + cidx;
+#pragma unroll
+                for (int q = 1; q < 19; q++)
+                    if ((mq >> q) & 1u) v[q] = C(Store<T>::ld(p + int64_t(dopp(q)) * n));
+            } else if (mq) {
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
 #pragma unroll
@@ -351,31 +357,20 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
 // Explosion (Eq. ctof): at the start of every visit of a finer level, each cell of its
 // explosion list takes all 19 values of its coarse parent's post-collision state, in the finer
 // level's current grid; cells of ghost layers 3-4 (never streamed) also in the other grid, which
-// the second sub-step reads.  The list holds whole 32-byte groups of a row; the extra cells are
-// never read.
+// the second sub-step reads.  The list holds whole 32-byte groups of a row (the extra cells are
+// never read) and the parent index of each entry; blockIdx.y is the direction, so every thread
+// moves one value.
 template <typename T>
-__global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c, int LB) {
+__global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= lv.necells) return;
+    const int q = blockIdx.y;
     const uint32_t e = uint32_t(__ldg(lv.ecells + i));
     const int c = int(e & 0x7FFFFFFFu);
-    const int B3s = 3 * LB, M = (1 << LB) - 1, B = 1 << LB;
-    const int g = c >> B3s, local = c & ((1 << B3s) - 1);
-    const int x = local & M, y = (local >> LB) & M, z = local >> (2 * LB);
-    const int pk = __ldg(lv.parent + g);
-    const int pb = pk >> 3, oct = pk & 7;
-    const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1, pz = ((oct >> 2) * B + z) >> 1;
-    const int pidx = (pb << B3s) + (pz << (2 * LB)) + (py << LB) + px;
-    const T* cf = static_cast<const T*>(co.f[cur_c]) + pidx;
-    T* f0 = static_cast<T*>(lv.f[cur]) + c;
-    T* f1 = static_cast<T*>(lv.f[cur ^ 1]) + c;
-    const bool both = e >> 31;
-#pragma unroll
-    for (int q = 0; q < 19; q++) {
-        const T v = cf[int64_t(q) * co.ncells];
-        f0[int64_t(q) * lv.ncells] = v;
-        if (both) f1[int64_t(q) * lv.ncells] = v;
-    }
+    const int pidx = __ldg(lv.eparent + i);
+    const T v = static_cast<const T*>(co.f[cur_c])[int64_t(q) * co.ncells + pidx];
+    static_cast<T*>(lv.f[cur])[int64_t(q) * lv.ncells + c] = v;
+    if (e >> 31) static_cast<T*>(lv.f[cur ^ 1])[int64_t(q) * lv.ncells + c] = v;
 }
 
 // Equilibrium start (Eq. fequ) followed by one collision, so the stored state is post-collision.
