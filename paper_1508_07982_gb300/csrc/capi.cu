@@ -5,7 +5,7 @@
 // levels).  Per coarse step, with F_L(s) the fused kernel of level L in its sub-step s and
 // E_L the explosion into level L's ghost layers:
 //     S(0) = [S(1)] F_0(1)      S(L) = E_L [S(L+1)] F_L(1) [S(L+1)] F_L(2)   (L >= 1)
-// E_L copies the coarse post-collision state into ghost layers 1-4 (Eq. ctof); F_L(1) carries
+// E_L copies the coarse post-collision state into ghost layers 1-3 (Eq. ctof); F_L(1) carries
 // stream, coalescence (reads of the finer ghost layers) and the second collision of Alg. 1;
 // F_L(2) carries the second stream and the first collision of the next visit.  Levels >= 1
 // flip their two-grid parity an even number of times per coarse step, level 0 once; the

@@ -6,7 +6,7 @@
 // leaf set this file derives what the GPU kernels need per level:
 //  - owned bricks (the level's leaves) and ghost bricks: block positions covered by the
 //    next coarser level that touch an owned brick; they hold the fine ghost layers of
-//    Sec. 4 (layers 1-2 are streamed, layers 3+ are read through the coarse parent);
+//    Sec. 4 (layers 1-2 are streamed, layer 3 holds the exploded coarse value);
 //  - a 27-entry neighbour table per brick (periodic axes wrap), parent links from ghost
 //    bricks to the coarse brick under them (explosion, Eq. ctof) and child links from owned
 //    bricks to the finer ghost bricks inside them (coalescence, Eq. ftoc);
@@ -260,7 +260,7 @@ struct Builder {
                         int g[3] = {P[0] * B + x, P[1] * B + y, P[2] * B + z};
                         uint8_t ck;
                         if (obstacle(L - 1, g[0] >> 1, g[1] >> 1, g[2] >> 1)) ck = CK_SOLID;
-                        else ck = dmin <= 2 ? CK_GHOST : (dmin <= 4 ? CK_G34 : CK_FAR);
+                        else ck = dmin <= 2 ? CK_GHOST : (dmin == 3 ? CK_G3 : CK_FAR);
                         int c = (z * B + y) * B + x;
                         cells[c] = ck;
                         if (ck == CK_GHOST) V.nghost12++;
@@ -275,7 +275,7 @@ struct Builder {
 
     // Link bits of cell (x, y, z) of brick k: bit q is set when pull q is not a plain load of a
     // stored value of this level (the source is an obstacle or lies beyond a wall, or, for owned
-    // cells, coalescence replaces the PDF).  With the explosion written into ghost layers 1-4 by
+    // cells, coalescence replaces the PDF).  With the explosion written into ghost layers 1-3 by
     // the coarser level, sources in ghost layers are stored values.
     uint32_t link_bits(const HostLevel& V, int k, int x, int y, int z, bool owned) const {
         const int B = p.B, B3 = B * B * B, M = B - 1;
@@ -289,7 +289,7 @@ struct Builder {
             bool plain = false;
             if (nb >= 0) {
                 uint8_t ck = V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)];
-                plain = ck == CK_FLUID || ck == CK_GHOST || ck == CK_G34;
+                plain = ck == CK_FLUID || ck == CK_GHOST || ck == CK_G3;
             }
             if (finer) {
                 bool coal = nb == NB_FINER;
@@ -303,21 +303,61 @@ struct Builder {
         return m;
     }
 
-    // True when every link in m pulls from an obstacle cell of this level that no coalescence
-    // replaces, so the pull is the cell's own opposite value (no-slip bounce-back, Sec. 2.2).
-    bool bounce_only(const HostLevel& V, int k, int x, int y, int z, uint32_t m) const {
+    // Wall face whose boundary condition a source beyond the domain takes: the first face it
+    // lies beyond in the order z+, z-, y+, y-, x+, x-.
+    int wall_face(const HostLevel& V, int k, int sx, int sy, int sz) const {
+        const int B = p.B;
+        const int g[3] = {V.pos[3 * k] * B + sx, V.pos[3 * k + 1] * B + sy, V.pos[3 * k + 2] * B + sz};
+        if (!p.per[2] && g[2] >= V.N[2]) return 5;
+        if (!p.per[2] && g[2] < 0) return 4;
+        if (!p.per[1] && g[1] >= V.N[1]) return 3;
+        if (!p.per[1] && g[1] < 0) return 2;
+        if (!p.per[0] && g[0] >= V.N[0]) return 1;
+        return 0;
+    }
+
+    // Fast-path bits of an owned cell's link mask m (Sec. 2.2, Eq. ftoc):
+    //  bit 29 + face in bits 25-27 when every marked link is a bounce-back of the cell's own
+    //  opposite value, from obstacle cells or from beyond one single wall face (7 = no wall);
+    //  an obstacle link next to a velocity wall is left to the general pull;
+    //  bit 28 when every marked link is a coalescence link.
+    uint32_t fast_bits(const HostLevel& V, int k, int x, int y, int z, uint32_t m) const {
         const int B = p.B, B3 = B * B * B, M = B - 1;
         const int32_t* nbr = &V.nbr[size_t(k) * 27];
-        if (V.kind[k] & BK_TOUCH_FINER) return false;
+        const bool finer = V.kind[k] & BK_TOUCH_FINER;
+        bool bounce = true, coal_all = finer;
+        int face = 7;
+        bool solid_seen = false;
         for (int q = 1; q < Q; q++) {
             if (!((m >> q) & 1u)) continue;
             int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
             for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
             int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
-            if (nb < 0) return false;
-            if (V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] != CK_SOLID) return false;
+            bool coal = false;
+            if (finer) {
+                coal = nb == NB_FINER;
+                if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
+                if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
+                if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
+            }
+            coal_all = coal_all && coal;
+            if (coal) {
+                bounce = false;
+            } else if (nb == NB_WALL) {
+                const int f = wall_face(V, k, s[0], s[1], s[2]);
+                if (face == 7) face = f;
+                else if (face != f) bounce = false;
+            } else if (nb >= 0 && V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] == CK_SOLID) {
+                solid_seen = true;
+            } else {
+                bounce = false;
+            }
         }
-        return true;
+        if (bounce && solid_seen && face != 7 && p.d.bc[face] == LBM_BC_VELOCITY) bounce = false;
+        uint32_t r = 0;
+        if (bounce) r |= (1u << 29) | (uint32_t(face) << 25);
+        if (coal_all) r |= 1u << 28;
+        return r;
     }
 
     // Owned cells: link bits and bit 31 for non-fluid cells; per owned column the bitmap of its
@@ -342,7 +382,7 @@ struct Builder {
                     for (int x = 0; x < B; x++) {
                         const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
                         uint32_t m = link_bits(V, k, x, y, z, true);
-                        if (m && bounce_only(V, k, x, y, z, m)) m |= 1u << 29;
+                        if (m) m |= fast_bits(V, k, x, y, z, m);
                         if (V.cell[c] != CK_FLUID) {
                             m |= 1u << 31;
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
@@ -360,7 +400,7 @@ struct Builder {
                         for (int x = x0; x < x0 + G; x++) {
                             const uint8_t ck = V.cell[row + x];
                             g12 = g12 || ck == CK_GHOST;
-                            g14 = g14 || ck == CK_GHOST || ck == CK_G34;
+                            g14 = g14 || ck == CK_GHOST || ck == CK_G3;
                         }
                         for (int x = x0; x < x0 + G && g12; x++) {
                             const int c = int(row + x);
@@ -369,7 +409,7 @@ struct Builder {
                         }
                         for (int x = x0; x < x0 + G && g14; x++) {
                             const int c = int(row + x);
-                            V.ecells.push_back(V.cell[c] == CK_G34 ? int32_t(uint32_t(c) | (1u << 31)) : c);
+                            V.ecells.push_back(V.cell[c] == CK_G3 ? int32_t(uint32_t(c) | (1u << 31)) : c);
                             const int pk = V.parent[k], pb = pk >> 3, oct = pk & 7;
                             const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1;
                             const int pz = ((oct >> 2) * B + z) >> 1;

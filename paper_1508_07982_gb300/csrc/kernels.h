@@ -31,7 +31,7 @@ struct DevLevel {
                           // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
     const uint32_t* glink;  // [ngcells] link bits of the ghost work list; bit 30 = copy only
     const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
-    const int32_t* ecells;     // explosion targets; bit 31 = ghost layers 3-4
+    const int32_t* ecells;     // explosion targets; bit 31 = ghost layer 3
     const int32_t* eparent;    // coarse parent cell of each explosion target
     int necells;
     int nown, nbricks, ngcells;
@@ -55,7 +55,8 @@ struct StepArgs {
 // Bits of the per-cell link mask.
 constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
 constexpr uint32_t LINK_COPY = 1u << 30;
-constexpr uint32_t LINK_BOUNCE_ONLY = 1u << 29;
+constexpr uint32_t LINK_BOUNCE_ONLY = 1u << 29;   // face of the wall term in bits 25-27
+constexpr uint32_t LINK_COAL_ONLY = 1u << 28;
 constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18
 
 // Launchers (one set per storage precision: 0 FP64, 1 FP32S, 2 FP16S).

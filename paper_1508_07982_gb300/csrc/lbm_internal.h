@@ -20,9 +20,9 @@ inline double weight(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 :
 enum : uint8_t {
     CK_FLUID = 0,  // owned fluid cell: collides and streams
     CK_GHOST = 1,  // fluid cell of ghost layers 1-2 (covered by the coarser level): streams only
-    CK_FAR = 2,    // fluid cell of ghost layer 5 or beyond: never read
+    CK_FAR = 2,    // fluid cell of ghost layer 4 or beyond: never read
     CK_SOLID = 3,  // no-slip obstacle
-    CK_G34 = 4,    // fluid cell of ghost layers 3-4: holds the exploded coarse value, never streamed
+    CK_G3 = 4,     // fluid cell of ghost layer 3: holds the exploded coarse value, never streamed
 };
 // Neighbour-table codes for block positions that hold no brick of this level.
 enum : int32_t { NB_WALL = -1, NB_FINER = -2, NB_COARSE = -3 };
@@ -45,11 +45,12 @@ struct HostLevel {
                                    // row that holds a ghost-layer-1/2 fluid cell
     std::vector<uint32_t> glink;   // [gcells] link bits; bit 30 = not a layer-1/2 fluid cell (copy)
     std::vector<int32_t> ecells;   // explosion targets: every cell of each 32-byte group of a row that
-                                   // holds a fluid cell of ghost layers 1-4; bit 31 = layers 3-4
+                                   // holds a fluid cell of ghost layers 1-3; bit 31 = layer 3
     std::vector<int32_t> eparent;  // [ecells] the coarse parent cell of each target on level L-1
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
-                                   // same-level load; bit 29 = every such link is a no-slip
-                                   // bounce-back from an obstacle cell; bit 31 = not fluid
+                                   // same-level load; bit 29 = every such link is a bounce-back
+                                   // (bits 25-27: wall face of its wall term, 7 = none); bit 28 =
+                                   // every such link is a coalescence link; bit 31 = not fluid
     std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
     int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells

@@ -160,7 +160,7 @@ template <> struct Par<float> {
 //   - obstacle or domain wall: bounce-back of the cell's own opposite value (Sec. 2.2), plus
 //     6 w rho0 e.u_w on velocity walls; a source beyond several faces takes the first of
 //     z+, z-, y+, y-, x+, x-;
-//   - otherwise the stored value of the source cell (owned, or ghost layers 1-4, which hold the
+//   - otherwise the stored value of the source cell (owned, or ghost layers 1-3, which hold the
 //     exploded coarse values or their first-sub-step stream).
 template <typename T, typename C, int LB>
 __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick, int x, int y, int z, int q,
@@ -188,7 +188,7 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
         const int64_t sidx = (int64_t(nb) << B3s) + ((sz & M) << (2 * LB)) + ((sy & M) << LB) + (sx & M);
         const uint8_t ck = __ldg(a.lv.cell + sidx);
         if (ck == CK_SOLID) return acc.load(src, n, qo, cidx);
-        if (ck == CK_FAR) return qnan<C>();
+        if (ck == CK_FAR) return qnan<C>();   // never a source: layer 4+ holds no value
         return acc.load(src, n, q, sidx);
     }
     if (nb == NB_WALL) {
@@ -282,11 +282,21 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             }
             const uint32_t mq = m & LINK_ALL;
             if (m & LINK_BOUNCE_ONLY) {
-                // every marked link bounces back from an obstacle: the cell's own opposite value
+                // every marked link bounces back: the cell's own opposite value, plus the wall
+                // term of one wall face (face 7: obstacle links only, no term)
                 const T* p = src + cidx;
+                const int face = int((m >> 25) & 7u);
 #pragma unroll
                 for (int q = 1; q < 19; q++)
-                    if ((mq >> q) & 1u) v[q] = C(Store<T>::ld(p + int64_t(dopp(q)) * n));
+                    if ((mq >> q) & 1u) {
+                        C t = C(Store<T>::ld(p + int64_t(dopp(q)) * n));
+                        if (face != 7) t += C(__ldg(a.wall + face * 19 + q));
+                        v[q] = t;
+                    }
+            } else if (m & LINK_COAL_ONLY) {
+#pragma unroll
+                for (int q = 1; q < 19; q++)
+                    if ((mq >> q) & 1u) v[q] = acc.children_mean(brick, x, y, z, q);
             } else if (mq) {
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     }
     const uint32_t gm = __ldg(a.lv.glink + i);
     if (gm & LINK_COPY) {
-        // not a layer-1/2 fluid cell: keep the stored value (layers 3-4 hold the exploded value)
+        // not a layer-1/2 fluid cell: keep the stored value (layer 3 holds the exploded value)
         const T* p = src + c;
         T* d = dst + c;
 #pragma unroll
@@ -356,10 +366,10 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
 
 // Explosion (Eq. ctof): at the start of every visit of a finer level, each cell of its
 // explosion list takes all 19 values of its coarse parent's post-collision state, in the finer
-// level's current grid; cells of ghost layers 3-4 (never streamed) also in the other grid, which
-// the second sub-step reads.  The list holds whole 32-byte groups of a row (the extra cells are
-// never read) and the parent index of each entry; blockIdx.y is the direction, so every thread
-// moves one value.
+// level's current grid; cells of ghost layer 3 (never streamed, read by layer 2) also in the other
+// grid, which the second sub-step reads.  Layer 4 is never read and is not written.  The list
+// holds whole 32-byte groups of a row (the extra cells are never read) and the parent index of
+// each entry; blockIdx.y is the direction, so every thread moves one value.
 template <typename T>
 __global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
