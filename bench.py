@@ -134,22 +134,33 @@ def _ncu_traffic(precision):
     return e.get("dram_bytes_per_launch")
 
 
-def _run_timed(lbm, torch, case, precision, steps, warmup, timing=True):
-    f = lbm.Forest(case, precision=precision)
-    f.init_uniform(case["u_init"])
-    f.step_coarse(warmup)
-    torch.cuda.synchronize()
+def _timed_graph(f, torch, steps):
+    """K coarse steps of graph replay on the current stream, timed with CUDA events."""
     stream = torch.cuda.current_stream()
-    if timing:
-        f.timing_begin(steps)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     f.step_coarse(steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    lev = f.timing_end(explode=True) if timing else None
+    return e0.elapsed_time(e1)
+
+
+def _timed_kernels(f, torch, steps):
+    """The same K coarse steps with a CUDA event between every pair of kernels (the launches are
+    enqueued directly in this mode); returns (total ms, per-level kernel times and counts)."""
+    f.timing_begin(steps)
+    ms = _timed_graph(f, torch, steps)
+    return ms, f.timing_end(explode=True)
+
+
+def _run_timed(lbm, torch, case, precision, steps, warmup):
+    f = lbm.Forest(case, precision=precision)
+    f.init_uniform(case["u_init"])
+    f.step_coarse(warmup)
+    torch.cuda.synchronize()
+    ms = _timed_graph(f, torch, steps)
+    _, lev = _timed_kernels(f, torch, steps)
     return f, ms, lev
 
 
@@ -306,7 +317,7 @@ def main():
     build.build()
     peaks, peak_kind = _measured_peaks()
 
-    # ---- timed region: K coarse steps of the resident workload, graph replay, events per kernel
+    # ---- timed region: K coarse steps of the resident workload, CUDA-graph replay
     f = lbm.Forest(case, precision=args.precision)
     f.init_uniform(case["u_init"])
     f.step_coarse(max(args.warmup, 3))
@@ -317,19 +328,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    stream = torch.cuda.current_stream()
-    f.timing_begin(args.steps)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    f.step_coarse(args.steps)
-    e1.record(stream)
+    ms = _timed_graph(f, torch, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    lev = f.timing_end(explode=True)
+    # per-kernel durations: a second timed pass of the same K steps with events between kernels
+    ms_k, lev = _timed_kernels(f, torch, args.steps)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -337,6 +342,7 @@ def main():
     upd = f.cell_updates_per_coarse_step()
     value = world * upd * args.steps / (ms / 1e3) / 1e9
     roof = _roofline(f, lev, args.precision, peaks, peak_kind)
+    roof["kernel_timing_pass_ms_per_step"] = round(ms_k / args.steps, 5)
     cfg = _config(case, f)
     mass = f.reduce_mass_momentum()
 

@@ -179,8 +179,8 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
 
 /* ---- measurement -------------------------------------------------------------------------
  * lbm_timing_begin(f, max_steps) makes the next lbm_step_coarse calls (at most max_steps
- * coarse steps in total) record CUDA events around every kernel of the captured graph, on the
- * forest's stream.  lbm_timing_end synchronises and returns, per level, the summed time in ms
+ * coarse steps in total) enqueue the step's kernels directly, with a CUDA event recorded on the
+ * forest's stream before and after every kernel (the same launches the captured graph holds).  lbm_timing_end synchronises and returns, per level, the summed time in ms
  * and the number of launches of the stream-collide kernels and of the explosion kernels
  * (arrays of length n_levels; any may be NULL), then stops timing. */
 lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);

@@ -49,6 +49,7 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
 struct Launch {
     int level, substep, grid;
     int type;   // 0: stream-collide F_L(substep), 1: explosion E_L
+    int lzc;    // log2 cells per thread along z of this level's stream-collide launch
 };
 
 struct DevBuf {
@@ -112,32 +113,25 @@ struct lbm_forest {
     unsigned init_mask = 0;
     bool params_set = false;
     std::vector<Launch> sched;
-    cudaGraph_t graph[2][2] = {};
-    cudaGraphExec_t exec[2][2] = {};
-    std::vector<cudaEvent_t> cap_events[2][2];
-    std::vector<cudaGraphNode_t> ev_nodes[2];
+    cudaGraph_t graph[2] = {};
+    cudaGraphExec_t exec[2] = {};
     bool timing = false;
     int tmax = 0, tused = 0;
     std::vector<cudaEvent_t> tev;
     int64_t updates = 0;
-    int lzc = 3;        // log2 of the cells per thread along z in the owned part of the step kernel
+    int lzc = 3;        // upper bound of log2 cells per thread along z (small levels use fewer)
     int minb = 3;       // CTAs per SM of the step-kernel variant
 };
 
 namespace {
 
 void free_graphs(lbm_forest* f) {
-    for (int t = 0; t < 2; t++)
-        for (int p = 0; p < 2; p++) {
-            if (f->exec[t][p]) cudaGraphExecDestroy(f->exec[t][p]);
-            if (f->graph[t][p]) cudaGraphDestroy(f->graph[t][p]);
-            f->exec[t][p] = nullptr;
-            f->graph[t][p] = nullptr;
-            for (cudaEvent_t e : f->cap_events[t][p]) cudaEventDestroy(e);
-            f->cap_events[t][p].clear();
-        }
-    f->ev_nodes[0].clear();
-    f->ev_nodes[1].clear();
+    for (int p = 0; p < 2; p++) {
+        if (f->exec[p]) cudaGraphExecDestroy(f->exec[p]);
+        if (f->graph[p]) cudaGraphDestroy(f->graph[p]);
+        f->exec[p] = nullptr;
+        f->graph[p] = nullptr;
+    }
 }
 
 void free_timing(lbm_forest* f) {
@@ -158,7 +152,7 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.cur_f = L + 1 < n ? cur[L + 1] : 0;
     a.substep = l.substep;
     a.LB = f->plan.LB;
-    a.lzc = f->lzc;
+    a.lzc = l.lzc;
     a.minb = f->minb;
     a.per = (f->plan.per[0] ? 1 : 0) | (f->plan.per[1] ? 2 : 0) | (f->plan.per[2] ? 4 : 0);
     a.params = f->d_params + L;
@@ -171,15 +165,24 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
 void build_schedule(lbm_forest* f) {
     f->sched.clear();
     const int n = f->plan.nlev, B = f->plan.B;
+    int sms = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     auto push = [&](int L, int s) {
         const HostLevel& V = f->plan.lv[L];
-        const int64_t units = int64_t(V.nown) * B * B * (B >> f->lzc);
+        // cells per thread: the largest power of two up to the configured bound that still gives
+        // about four waves of CTAs on this level
+        int lzc = f->lzc;
+        while (lzc > 0 && int64_t(V.nown) * B * B * (B >> lzc) / 256 < int64_t(4) * sms * f->minb) lzc--;
+        const int64_t units = int64_t(V.nown) * B * B * (B >> lzc);
         int grid = int((units + 255) / 256) + int((V.gcells.size() + 255) / 256);
-        f->sched.push_back({L, s, grid, 0});
+        f->sched.push_back({L, s, grid, 0, lzc});
     };
     auto explode = [&](int L) {
         const HostLevel& V = f->plan.lv[L];
-        f->sched.push_back({L, 0, int((V.ecells.size() + 255) / 256), 1});
+        f->sched.push_back({L, 0, int((V.ecells.size() + 255) / 256), 1, 0});
     };
     std::function<void(int)> rec = [&](int L) {
         if (L == 0) {
@@ -196,29 +199,30 @@ void build_schedule(lbm_forest* f) {
     rec(0);
 }
 
-lbm_status capture(lbm_forest* f, int timed, int parity) {
-    int cur[LBM_MAX_LEVELS];
-    std::memcpy(cur, f->cur, sizeof cur);
-    cur[0] = parity;
-    std::vector<cudaEvent_t>& evs = f->cap_events[timed][parity];
-    if (timed) {
-        evs.resize(f->sched.size() + 1);
-        for (auto& e : evs) CU(cudaEventCreate(&e));
-    }
-    cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal));
+// Enqueues every kernel of one coarse step on stream s; cur holds the two-grid parity of each
+// level and is advanced.  With events, evs[k] is recorded before launch k and evs[k+1] after.
+void enqueue_step(lbm_forest* f, cudaStream_t s, int* cur, cudaEvent_t* evs) {
     for (size_t k = 0; k < f->sched.size(); k++) {
         const Launch& l = f->sched[k];
-        if (timed) CU(cudaEventRecordWithFlags(evs[k], f->cap, cudaEventRecordExternal));
+        if (evs) cudaEventRecord(evs[k], s);
         if (l.type == 1) {
-            f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], f->plan.LB, f->cap);
+            f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], f->plan.LB, s);
             continue;
         }
         StepArgs a = make_args(f, l, cur);
-        f->L->step(a, f->plan.d.collision, l.grid, f->cap);
+        f->L->step(a, f->plan.d.collision, l.grid, s);
         cur[l.level] ^= 1;
     }
-    if (timed) CU(cudaEventRecordWithFlags(evs.back(), f->cap, cudaEventRecordExternal));
+    if (evs) cudaEventRecord(evs[f->sched.size()], s);
+}
+
+lbm_status capture(lbm_forest* f, int parity) {
+    int cur[LBM_MAX_LEVELS];
+    std::memcpy(cur, f->cur, sizeof cur);
+    cur[0] = parity;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(f, f->cap, cur, nullptr);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(f->cap, &g);
     if (le != cudaSuccess) {
@@ -226,26 +230,8 @@ lbm_status capture(lbm_forest* f, int timed, int parity) {
         return fail(LBM_ECUDA, "kernel launch during capture failed: %s", cudaGetErrorString(le));
     }
     if (ce != cudaSuccess) return fail(LBM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
-    f->graph[timed][parity] = g;
-    CU(cudaGraphInstantiate(&f->exec[timed][parity], g, 0));
-    if (timed) {
-        size_t nn = 0;
-        CU(cudaGraphGetNodes(g, nullptr, &nn));
-        std::vector<cudaGraphNode_t> nodes(nn);
-        CU(cudaGraphGetNodes(g, nodes.data(), &nn));
-        f->ev_nodes[parity].assign(evs.size(), nullptr);
-        for (cudaGraphNode_t nd : nodes) {
-            cudaGraphNodeType t;
-            CU(cudaGraphNodeGetType(nd, &t));
-            if (t != cudaGraphNodeTypeEventRecord) continue;
-            cudaEvent_t e;
-            CU(cudaGraphEventRecordNodeGetEvent(nd, &e));
-            for (size_t k = 0; k < evs.size(); k++)
-                if (evs[k] == e) f->ev_nodes[parity][k] = nd;
-        }
-        for (cudaGraphNode_t nd : f->ev_nodes[parity])
-            if (!nd) return fail(LBM_ECUDA, "timing event node missing from the captured graph");
-    }
+    f->graph[parity] = g;
+    CU(cudaGraphInstantiate(&f->exec[parity], g, 0));
     return LBM_OK;
 }
 
@@ -572,19 +558,23 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
     if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
         return fail(LBM_EINVAL, "set the level parameters and initialise every level before stepping");
     for (int i = 0; i < n_steps; i++) {
+        if (f->timing && f->tused < f->tmax) {
+            // measured steps: the same launches, enqueued directly with an event between each
+            // pair (host work per step is far below the step's GPU time)
+            int cur[LBM_MAX_LEVELS];
+            std::memcpy(cur, f->cur, sizeof cur);
+            enqueue_step(f, f->stream, cur, &f->tev[size_t(f->tused) * (f->sched.size() + 1)]);
+            CU(cudaGetLastError());
+            f->tused++;
+            f->cur[0] ^= 1;
+            continue;
+        }
         const int p = f->cur[0];
-        const int timed = f->timing && f->tused < f->tmax ? 1 : 0;
-        if (!f->exec[timed][p]) {
-            lbm_status s = capture(f, timed, p);
+        if (!f->exec[p]) {
+            lbm_status s = capture(f, p);
             if (s) return s;
         }
-        if (timed) {
-            const size_t ne = f->ev_nodes[p].size();
-            for (size_t k = 0; k < ne; k++)
-                CU(cudaGraphExecEventRecordNodeSetEvent(f->exec[1][p], f->ev_nodes[p][k], f->tev[f->tused * ne + k]));
-            f->tused++;
-        }
-        CU(cudaGraphLaunch(f->exec[timed][p], f->stream));
+        CU(cudaGraphLaunch(f->exec[p], f->stream));
         f->cur[0] ^= 1;
     }
     return LBM_OK;
