@@ -54,6 +54,16 @@ template <typename C> __device__ __forceinline__ C qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000ULL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
+// ------------------------------------------------------------------ shared-memory staging
+// 4-byte asynchronous copies global -> shared (LDGSTS); a false predicate zero-fills without
+// reading global memory.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(pred ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
 // v holds f (or f - w rho0 when shifted) on entry and f-tilde on exit.  R is rho (or rho - rho0).
 // SRT: f~ = f - omega (f - f^eq) + F;  TRT: f~ = f - le (f+ - f^eq+) - lo (f- - f^eq-) + F, with
@@ -216,7 +226,10 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
 template <typename T, typename C, int COLL, int LB, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
-    __shared__ C slow[19][256];
+    // FP32 storage stages each cell's 19 pulls in shared memory with cp.async, two cells deep;
+    // the other storage types load into registers.  The same array receives general-pull values.
+    constexpr bool kAsync = sizeof(T) == 4;
+    __shared__ C slow[kAsync ? 2 : 1][19][256];
     const int zc = 1 << a.lzc;
     const int upb = (1 << B2s) << (LB - a.lzc);            // units (column chunks) per brick
     const int64_t owned_units = int64_t(a.lv.nown) * upb;
@@ -248,38 +261,27 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             const int nb = (ox | oy) ? __ldg(nbr + 13 + ox + 3 * oy) : brick;
             off[q] = (max(nb, 0) << B3s) + ((sy & M) << LB) + (sx & M) - dez(q) * (1 << B2s);
         }
+        // source index of pull q into the cell at height z; on the brick's z faces the links
+        // that leave the brick read the z-neighbour brick (z is uniform in a warp)
+        auto src_index = [&](int q, int z) -> int {
+            int sidx = off[q] + (z << B2s);
+            if ((dez(q) == 1 && z == 0) || (dez(q) == -1 && z == M)) {
+                const int sx = x - dex(q), sy = y - dey(q), oz = dez(q) == 1 ? -1 : 1;
+                const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+                const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+                const int nb = __ldg(nbr + 13 + ox + 3 * oy + 9 * oz);
+                sidx = (max(nb, 0) << B3s) + ((oz < 0 ? M : 0) << B2s) + ((sy & M) << LB) + (sx & M);
+            }
+            return sidx;
+        };
         const uint32_t solid = need_mask ? __ldg(a.lv.colsolid + (brick << B2s) + col) : 0u;
         const LevelParams* P = a.params;
         const C le = Par<C>::le(P), lo = Par<C>::lo(P);
         const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
         const C rho0 = C(a.rho0), inv_rho0 = C(a.inv_rho0);
-        for (int k = 0; k < zc; k++) {
-            const int z = z0 + k;
-            const int zoff = z << B2s;
-            const int cidx = (brick << B3s) + zoff + (y << LB) + x;
-            if ((solid >> z) & 1u) continue;
-            // The loads do not wait for the link mask: every address below lies inside the level's
-            // grid, and the links the mask marks are replaced afterwards.  On the brick's z faces
-            // the links that leave the brick read the z-neighbour brick (z is uniform in a warp).
-            const uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
-            C v[19];
-            {
-                const T* p = src;
-                v[0] = C(Store<T>::ld(p + cidx));
-#pragma unroll
-                for (int q = 1; q < 19; q++) {
-                    p += n;
-                    int s = off[q] + zoff;
-                    if ((dez(q) == 1 && z == 0) || (dez(q) == -1 && z == M)) {
-                        const int sx = x - dex(q), sy = y - dey(q), oz = dez(q) == 1 ? -1 : 1;
-                        const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
-                        const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
-                        const int nb = __ldg(nbr + 13 + ox + 3 * oy + 9 * oz);
-                        s = (max(nb, 0) << B3s) + ((oz < 0 ? M : 0) << B2s) + ((sy & M) << LB) + (sx & M);
-                    }
-                    v[q] = C(Store<T>::ld(p + s));
-                }
-            }
+        // Links the link mask marks are replaced after the plain pulls (every plain address lies
+        // inside the level's grid, so nothing waits for the mask).
+        auto finish = [&](int z, int cidx, uint32_t m, C (&v)[19], C (&buf)[19][256]) {
             const uint32_t mq = m & LINK_ALL;
             if (m & LINK_BOUNCE_ONLY) {
                 // every marked link bounces back: the cell's own opposite value, plus the wall
@@ -299,19 +301,66 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
                     if ((mq >> q) & 1u) v[q] = acc.children_mean(brick, x, y, z, q);
             } else if (mq) {
                 for (int q = 1; q < 19; q++)
-                    if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
+                    if ((mq >> q) & 1u) buf[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
 #pragma unroll
                 for (int q = 1; q < 19; q++)
-                    if ((mq >> q) & 1u) v[q] = slow[q][tid];
+                    if ((mq >> q) & 1u) v[q] = buf[q][tid];
             }
             collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0);
-            {
-                T* p = dst + cidx;
+            T* p = dst + cidx;
 #pragma unroll
-                for (int q = 0; q < 19; q++) {
-                    Store<T>::st(p, v[q]);
+            for (int q = 0; q < 19; q++) {
+                Store<T>::st(p, v[q]);
+                p += n;
+            }
+        };
+        if constexpr (kAsync) {
+            // two-deep pipeline: the pulls of cell k+1 are in flight while cell k collides
+            auto issue = [&](int k) -> uint32_t {
+                const int z = z0 + k;
+                const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
+                const bool live = !((solid >> z) & 1u);
+                C(&stage)[19][256] = slow[k & 1];
+                const T* p = src;
+                cp_async4(&stage[0][tid], p + cidx, live);
+#pragma unroll
+                for (int q = 1; q < 19; q++) {
                     p += n;
+                    cp_async4(&stage[q][tid], p + src_index(q, z), live);
                 }
+                cp_async_commit();
+                return (need_mask && live) ? __ldg(a.lv.link + cidx) : 0u;
+            };
+            uint32_t m_next = issue(0);
+            for (int k = 0; k < zc; k++) {
+                const uint32_t m = m_next;
+                if (k + 1 < zc) m_next = issue(k + 1);
+                else cp_async_commit();
+                cp_async_wait1();
+                const int z = z0 + k;
+                if ((solid >> z) & 1u) continue;
+                const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
+                C(&stage)[19][256] = slow[k & 1];
+                C v[19];
+#pragma unroll
+                for (int q = 0; q < 19; q++) v[q] = stage[q][tid];
+                finish(z, cidx, m, v, stage);
+            }
+        } else {
+            for (int k = 0; k < zc; k++) {
+                const int z = z0 + k;
+                const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
+                if ((solid >> z) & 1u) continue;
+                const uint32_t m = need_mask ? __ldg(a.lv.link + cidx) : 0u;
+                C v[19];
+                const T* p = src;
+                v[0] = C(Store<T>::ld(p + cidx));
+#pragma unroll
+                for (int q = 1; q < 19; q++) {
+                    p += n;
+                    v[q] = C(Store<T>::ld(p + src_index(q, z)));
+                }
+                finish(z, cidx, m, v, slow[0]);
             }
         }
         return;
@@ -351,10 +400,10 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     const uint32_t mq = gm & LINK_ALL;
     if (mq) {
         for (int q = 1; q < 19; q++)
-            if ((mq >> q) & 1u) slow[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
+            if ((mq >> q) & 1u) slow[0][q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
 #pragma unroll
         for (int q = 1; q < 19; q++)
-            if ((mq >> q) & 1u) v[q] = slow[q][tid];
+            if ((mq >> q) & 1u) v[q] = slow[0][q][tid];
     }
     T* p = dst + c;
 #pragma unroll
