@@ -60,6 +60,7 @@ struct DevBuf {
     uint32_t* link = nullptr;
     uint32_t* glink = nullptr;
     uint32_t* colsolid = nullptr;
+    uint8_t* colspec = nullptr;
     int32_t* ecells = nullptr;
     int32_t* eparent = nullptr;
 };
@@ -346,6 +347,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.link);
         cudaFree(b.glink);
         cudaFree(b.colsolid);
+        cudaFree(b.colspec);
         cudaFree(b.ecells);
         cudaFree(b.eparent);
     }
@@ -398,7 +400,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
             (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)) ||
-            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.ecells, V.ecells)) ||
+            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.colspec, V.colspec)) || (s = upload(&b.ecells, V.ecells)) ||
             (s = upload(&b.eparent, V.eparent)))
             return bail(s);
         DevLevel& g = f->dl[L];
@@ -414,6 +416,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.link = b.link;
         g.glink = b.glink;
         g.colsolid = b.colsolid;
+        g.colspec = b.colspec;
         g.ecells = b.ecells;
         g.eparent = b.eparent;
         g.necells = int(V.ecells.size());

@@ -376,6 +376,7 @@ struct Builder {
         }
         V.link.assign(size_t(V.nown) * B3, 0u);
         V.colsolid.assign(size_t(V.nown) * B * B, 0u);
+        V.colspec.assign(size_t(V.nown) * B * B, 0);
         for (int k = 0; k < V.nown; k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
@@ -388,6 +389,7 @@ struct Builder {
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
                         }
                         V.link[c] = m;
+                        if (m) V.colspec[size_t(k) * B * B + size_t(y) * B + x] = 1;
                     }
         const int esize = p.d.precision == LBM_FP64 ? 8 : (p.d.precision == LBM_FP32S ? 4 : 2);
         const int G = std::min(32 / esize, B);

@@ -31,6 +31,7 @@ struct DevLevel {
                           // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
     const uint32_t* glink;  // [ngcells] link bits of the ghost work list; bit 30 = copy only
     const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
+    const uint8_t* colspec;    // [nown * B^2] per owned column: 1 if any cell has a nonzero link mask
     const int32_t* ecells;     // explosion targets; bit 31 = ghost layer 3
     const int32_t* eparent;    // coarse parent cell of each explosion target
     int necells;

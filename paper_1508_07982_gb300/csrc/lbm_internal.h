@@ -52,6 +52,7 @@ struct HostLevel {
                                    // (bits 25-27: wall face of its wall term, 7 = none); bit 28 =
                                    // every such link is a coalescence link; bit 31 = not fluid
     std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
+    std::vector<uint8_t> colspec;    // [nown * B^2] 1 if any cell of the column has a nonzero link mask
     int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }

@@ -54,6 +54,14 @@ template <typename C> __device__ __forceinline__ C qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000ULL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
+// Knuth's TwoSum: s = fl(a + b) and e with a + b = s + e exactly (round-to-nearest FP32).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
 // ------------------------------------------------------------------ shared-memory staging
 // 4-byte asynchronous copies global -> shared (LDGSTS); a false predicate zero-fills without
 // reading global memory.
@@ -128,7 +136,12 @@ struct Access {
         return C(Store<T>::ld(static_cast<const T*>(base) + int64_t(q) * n + idx));
     }
     // Mean of the 8 finer children of owned cell (x, y, z) of brick b after both fine sub-steps
-    // (coalescence, Eq. ftoc), summed pairwise in FP64 in z-y-x bit order.
+    // (coalescence, Eq. ftoc), summed pairwise in z-y-x bit order.  With FP64 storage the sum is
+    // FP64.  With FP32/FP16 storage it is an FP32 double-word sum (Knuth's TwoSum at every
+    // addition, the rounding errors carried in a second word): the children are FP32/FP16
+    // values, so this carries the exact sum as the FP64 accumulation would, up to the final
+    // rounding, while using the FP32 pipe (GB300 runs FP64 at a small fraction of FP32 rate,
+    // and coalescing cells are often isolated lanes of a warp).
     __device__ __forceinline__ C children_mean(int b, int x, int y, int z, int q) const {
         const int oct = ((2 * x) >> LB) | (((2 * y) >> LB) << 1) | (((2 * z) >> LB) << 2);
         const int cb = __ldg(a.lv.child + b * 8 + oct);
@@ -136,18 +149,23 @@ struct Access {
         const int cx = (2 * x) & M, cy = (2 * y) & M, cz = (2 * z) & M;
         const int64_t base = (int64_t(cb) << (3 * LB)) + (cz << (2 * LB)) + (cy << LB) + cx;
         const int sy = 1 << LB, sz = 1 << (2 * LB);
-        const void* f = a.fi.f[a.cur_f];
-        const int64_t n = a.fi.ncells;
-        double c0 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base));
-        double c1 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + 1));
-        double c2 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sy));
-        double c3 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sy + 1));
-        double c4 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sz));
-        double c5 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sz + 1));
-        double c6 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sz + sy));
-        double c7 = double(Store<T>::ld(static_cast<const T*>(f) + int64_t(q) * n + base + sz + sy + 1));
-        const double s = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
-        return C(s * 0.125);
+        const T* f = static_cast<const T*>(a.fi.f[a.cur_f]) + int64_t(q) * a.fi.ncells + base;
+        const C c0 = C(Store<T>::ld(f)), c1 = C(Store<T>::ld(f + 1));
+        const C c2 = C(Store<T>::ld(f + sy)), c3 = C(Store<T>::ld(f + sy + 1));
+        const C c4 = C(Store<T>::ld(f + sz)), c5 = C(Store<T>::ld(f + sz + 1));
+        const C c6 = C(Store<T>::ld(f + sz + sy)), c7 = C(Store<T>::ld(f + sz + sy + 1));
+        if constexpr (sizeof(C) == 8) {
+            const C s = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
+            return s * C(0.125);
+        } else {
+            float e01, e23, e45, e67, e03, e47, e07;
+            const float s01 = two_sum(c0, c1, e01), s23 = two_sum(c2, c3, e23);
+            const float s45 = two_sum(c4, c5, e45), s67 = two_sum(c6, c7, e67);
+            const float s03 = two_sum(s01, s23, e03), s47 = two_sum(s45, s67, e47);
+            const float s07 = two_sum(s03, s47, e07);
+            const float err = ((e01 + e23) + (e45 + e67)) + (e03 + e47) + e07;
+            return (s07 + err) * 0.125f;
+        }
     }
 };
 
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
         const int z0 = (r >> B2s) << a.lzc;
         const uint8_t bk = __ldg(a.lv.kind + brick);
         const int* nbr = a.lv.nbr + brick * 27;
-        const bool need_mask = !(bk & BK_PLAIN);
+        const bool need_mask = !(bk & BK_PLAIN) && __ldg(a.lv.colspec + (brick << B2s) + col);
         // source offsets of a cell inside the brick along z (in-plane neighbour bricks resolved)
         int off[19];
 #pragma unroll
