@@ -361,8 +361,8 @@ struct Builder {
     }
 
     // Owned cells: link bits and bit 31 for non-fluid cells; per owned column the bitmap of its
-    // non-fluid cells.  Ghost bricks: the stream and explosion work lists, in whole 32-byte groups
-    // of a row (group = 32 bytes / PDF size cells) so that every write covers full sectors.
+    // non-fluid cells and whether any of its cells has a nonzero link mask.  Ghost bricks: the
+    // stream and explosion work lists.
     void links(int L) {
         HostLevel& V = p.lv[L];
         const int B = p.B, B3 = B * B * B;
@@ -391,27 +391,20 @@ struct Builder {
                         V.link[c] = m;
                         if (m) V.colspec[size_t(k) * B * B + size_t(y) * B + x] = 1;
                     }
-        const int esize = p.d.precision == LBM_FP64 ? 8 : (p.d.precision == LBM_FP32S ? 4 : 2);
-        const int G = std::min(32 / esize, B);
+        // ghost work lists in cell order: the ghost-layer-1/2 fluid cells (stream) and the fluid
+        // cells of layers 1-3 (explosion targets)
         for (int k = V.nown; k < V.nbricks(); k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
-                    for (int x0 = 0; x0 < B; x0 += G) {
-                        const size_t row = size_t(k) * B3 + (size_t(z) * B + y) * B;
-                        bool g12 = false, g14 = false;
-                        for (int x = x0; x < x0 + G; x++) {
-                            const uint8_t ck = V.cell[row + x];
-                            g12 = g12 || ck == CK_GHOST;
-                            g14 = g14 || ck == CK_GHOST || ck == CK_G3;
-                        }
-                        for (int x = x0; x < x0 + G && g12; x++) {
-                            const int c = int(row + x);
+                    for (int x = 0; x < B; x++) {
+                        const int c = int(size_t(k) * B3 + (size_t(z) * B + y) * B + x);
+                        const uint8_t ck = V.cell[c];
+                        if (ck == CK_GHOST) {
                             V.gcells.push_back(c);
-                            V.glink.push_back(V.cell[c] == CK_GHOST ? link_bits(V, k, x, y, z, false) : (1u << 30));
+                            V.glink.push_back(link_bits(V, k, x, y, z, false));
                         }
-                        for (int x = x0; x < x0 + G && g14; x++) {
-                            const int c = int(row + x);
-                            V.ecells.push_back(V.cell[c] == CK_G3 ? int32_t(uint32_t(c) | (1u << 31)) : c);
+                        if (ck == CK_GHOST || ck == CK_G3) {
+                            V.ecells.push_back(ck == CK_G3 ? int32_t(uint32_t(c) | (1u << 31)) : c);
                             const int pk = V.parent[k], pb = pk >> 3, oct = pk & 7;
                             const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1;
                             const int pz = ((oct >> 2) * B + z) >> 1;

@@ -29,7 +29,7 @@ struct DevLevel {
     const int32_t* gcells;
     const uint32_t* link; // [nown * B^3] per owned cell: bit q set = link q needs the general pull;
                           // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
-    const uint32_t* glink;  // [ngcells] link bits of the ghost work list; bit 30 = copy only
+    const uint32_t* glink;  // [ngcells] link bits of the ghost work list
     const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
     const uint8_t* colspec;    // [nown * B^2] per owned column: 1 if any cell has a nonzero link mask
     const int32_t* ecells;     // explosion targets; bit 31 = ghost layer 3
@@ -55,7 +55,6 @@ struct StepArgs {
 
 // Bits of the per-cell link mask.
 constexpr uint32_t LINK_NOT_FLUID = 1u << 31;
-constexpr uint32_t LINK_COPY = 1u << 30;
 constexpr uint32_t LINK_BOUNCE_ONLY = 1u << 29;   // face of the wall term in bits 25-27
 constexpr uint32_t LINK_COAL_ONLY = 1u << 28;
 constexpr uint32_t LINK_ALL = 0x7FFFEu;   // directions 1..18

@@ -41,11 +41,10 @@ struct HostLevel {
     std::vector<int32_t> child;    // [nown][8] ghost brick of L+1 under each octant, or -1
     std::vector<uint8_t> kind;     // [nbricks] BK_* bits
     std::vector<uint8_t> cell;     // [nbricks * B^3] CK_* per cell
-    std::vector<int32_t> gcells;   // ghost stream work list: every cell of each 32-byte group of a
-                                   // row that holds a ghost-layer-1/2 fluid cell
-    std::vector<uint32_t> glink;   // [gcells] link bits; bit 30 = not a layer-1/2 fluid cell (copy)
-    std::vector<int32_t> ecells;   // explosion targets: every cell of each 32-byte group of a row that
-                                   // holds a fluid cell of ghost layers 1-3; bit 31 = layer 3
+    std::vector<int32_t> gcells;   // ghost stream work list: the fluid cells of ghost layers 1-2
+    std::vector<uint32_t> glink;   // [gcells] link bits
+    std::vector<int32_t> ecells;   // explosion targets: the fluid cells of ghost layers 1-3;
+                                   // bit 31 = layer 3
     std::vector<int32_t> eparent;  // [ecells] the coarse parent cell of each target on level L-1
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
                                    // same-level load; bit 29 = every such link is a bounce-back

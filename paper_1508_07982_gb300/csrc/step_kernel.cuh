@@ -240,7 +240,7 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
 // of one (x, y) column of a brick; the source offsets of a cell inside the brick are computed once
 // per column, obstacle cells are skipped by a per-column bitmap, and a per-cell link mask (read
 // where the brick needs it) routes the few links that are not plain loads to pull_general.  CTAs
-// after the owned part cover the ghost work list, in whole 32-byte groups.
+// after the owned part cover the ghost work list.
 template <typename T, typename C, int COLL, int LB, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
@@ -406,16 +406,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
             v[q] = C(Store<T>::ld(p + sidx));
         }
     }
-    const uint32_t gm = __ldg(a.lv.glink + i);
-    if (gm & LINK_COPY) {
-        // not a layer-1/2 fluid cell: keep the stored value (layer 3 holds the exploded value)
-        const T* p = src + c;
-        T* d = dst + c;
-#pragma unroll
-        for (int q = 0; q < 19; q++) d[int64_t(q) * n] = p[int64_t(q) * n];
-        return;
-    }
-    const uint32_t mq = gm & LINK_ALL;
+    const uint32_t mq = __ldg(a.lv.glink + i) & LINK_ALL;
     if (mq) {
         for (int q = 1; q < 19; q++)
             if ((mq >> q) & 1u) slow[0][q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
@@ -435,8 +426,8 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
 // explosion list takes all 19 values of its coarse parent's post-collision state, in the finer
 // level's current grid; cells of ghost layer 3 (never streamed, read by layer 2) also in the other
 // grid, which the second sub-step reads.  Layer 4 is never read and is not written.  The list
-// holds whole 32-byte groups of a row (the extra cells are never read) and the parent index of
-// each entry; blockIdx.y is the direction, so every thread moves one value.
+// holds the parent index of each entry; blockIdx.y is the direction, so every thread moves one
+// value.
 template <typename T>
 __global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
