@@ -57,7 +57,7 @@ def _pair(lbm, oracle_mod, case, precision="fp64", field=None, refine=None, flag
 
 
 def test_block_tables_match_the_oracle(lbm, oracle_mod):
-    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True)
     f = lbm.Forest(case)
     o = oracle_mod.Oracle(case)
     assert f.nlev == o.nlev == 4
@@ -100,7 +100,7 @@ def test_three_level_periodic_fp64_matches_the_oracle(lbm, oracle_mod, B):
 def test_sphere_channel_fp64_matches_the_oracle(lbm, oracle_mod):
     """The sphere-channel workload at H = 32 with B = 8: four levels, velocity inlet/outlet,
     periodic sides, a no-slip sphere on the finest level, uniform plug start."""
-    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True)
     f, o = _pair(lbm, oracle_mod, case)
     assert f.nlev == 4
     f.step_coarse(6)
@@ -164,7 +164,7 @@ def test_stepping_one_at_a_time_equals_stepping_in_one_call(lbm):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32s", "fp16s"])
 def test_checkpoint_resume_is_bit_exact(lbm, precision):
-    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True)
     a = lbm.Forest(case, precision=precision)
     a.init_uniform(case["u_init"])
     a.step_coarse(3)
@@ -232,3 +232,54 @@ def test_thread_mapping_does_not_change_results(lbm):
         else:
             for L in range(f.nlev):
                 assert np.array_equal(out[L], ref[L], equal_nan=True)
+
+
+def test_periodic_sphere_channel_matches_the_oracle(lbm, oracle_mod):
+    """The benchmark workload's geometry and boundaries (periodic faces, plug start) at H = 32."""
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    f, o = _pair(lbm, oracle_mod, case)
+    assert f.nlev == 4
+    f.step_coarse(8)
+    o.step(8)
+    assert _compare(f, o) < TOL64
+
+
+def _mirror_gap(f, level, axis):
+    """max |u(p) - M u(M p)| over owned fluid cells for the mirror M that flips `axis` about the
+    domain centre (the sphere centre lies on both the y and the z mid-plane)."""
+    rho, u = f.get_macroscopic(level)
+    X, Y, Z = f.cell_coords(level)
+    coords = [X, Y, Z]
+    N = {1: 64 << level, 2: 64 << level}[axis]
+    key = {}
+    for i in range(X.size):
+        key[(X[i], Y[i], Z[i])] = i
+    idx = np.arange(X.size)
+    mc = list(coords)
+    mc[axis] = N - 1 - coords[axis]
+    j = np.array([key[(a, b, c)] for a, b, c in zip(mc[0], mc[1], mc[2])])
+    ok = np.isfinite(rho)
+    um = u.copy()
+    um[axis] = -um[axis]
+    return float(np.abs(u[:, ok] - um[:, j][:, ok]).max())
+
+
+def test_full_size_bench_workload_conserves_mass_and_symmetry(lbm):
+    """Bench workload at full size (8.39M cells, 4 levels, 32^3 blocks) in FP64, in the launch
+    configuration bench.py times: total mass is conserved to round-off and the flow stays
+    mirror-symmetric about the y and z mid-planes; FP32 storage conserves mass to 1e-6."""
+    case = inputs.sphere_channel_case()
+    f = lbm.Forest(case, precision="fp64")
+    f.init_uniform(case["u_init"])
+    m0 = f.reduce_mass_momentum()
+    f.step_coarse(40)
+    m1 = f.reduce_mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
+    assert _mirror_gap(f, 1, 1) < 1e-12 and _mirror_gap(f, 1, 2) < 1e-12
+    f.close()
+    g = lbm.Forest(case, precision="fp32s")
+    g.init_uniform(case["u_init"])
+    m0 = g.reduce_mass_momentum()
+    g.step_coarse(40)
+    m1 = g.reduce_mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-6

@@ -56,7 +56,7 @@ def test_invalid_descriptions_are_rejected_on_the_host(lbm):
 
 def _cases():
     yield "cavity", inputs.cavity_case(), None
-    yield "channel", inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5)), None
+    yield "channel", inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True), None
     yield "poiseuille", inputs.plane_poiseuille_case(B=8, where="both"), None
     yield "periodic-ball", inputs.periodic_case(n=64, B=8, collision="trt", omega=1.7,
                                                 regions=[("ball", 3, (5, 60, 33), 9.0)], lmax=3), None
