@@ -245,19 +245,18 @@ def test_periodic_sphere_channel_matches_the_oracle(lbm, oracle_mod):
 
 
 def _mirror_gap(f, level, axis):
-    """max |u(p) - M u(M p)| over owned fluid cells for the mirror M that flips `axis` about the
-    domain centre (the sphere centre lies on both the y and the z mid-plane)."""
+    """max |u(p) - M u(M p)| over owned fluid cells for the mirror M that flips `axis` (1 = y,
+    2 = z) about the domain centre, on which the sphere centre lies."""
     rho, u = f.get_macroscopic(level)
     X, Y, Z = f.cell_coords(level)
-    coords = [X, Y, Z]
-    N = {1: 64 << level, 2: 64 << level}[axis]
-    key = {}
-    for i in range(X.size):
-        key[(X[i], Y[i], Z[i])] = i
-    idx = np.arange(X.size)
-    mc = list(coords)
-    mc[axis] = N - 1 - coords[axis]
-    j = np.array([key[(a, b, c)] for a, b, c in zip(mc[0], mc[1], mc[2])])
+    n = [(256 << level), (64 << level), (64 << level)]
+    key = (Z.astype(np.int64) * n[1] + Y) * n[0] + X
+    c = [X.copy(), Y.copy(), Z.copy()]
+    c[axis] = n[axis] - 1 - c[axis]
+    mkey = (c[2].astype(np.int64) * n[1] + c[1]) * n[0] + c[0]
+    order = np.argsort(key)
+    j = order[np.searchsorted(key[order], mkey)]
+    assert (key[j] == mkey).all()
     ok = np.isfinite(rho)
     um = u.copy()
     um[axis] = -um[axis]
