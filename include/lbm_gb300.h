@@ -108,12 +108,18 @@ lbm_status lbm_lattice(int32_t* e, double* w, int32_t* opp);
  * edges and corners, Sec. 3.2-3.3), the per-level block tables and the cell classes, without
  * touching a GPU.  lbm_plan_leaves writes the level's leaf blocks as (bx, by, bz) triples in
  * block-table order (pass NULL to query the count into *n).  lbm_plan_counts writes
- * {leaf blocks, owned fluid cells, ghost-layer-1/2 fluid cells, ghost blocks}. */
+ * {leaf blocks, owned fluid cells, ghost-layer-1/2 fluid cells, ghost blocks}.
+ * lbm_plan_ghost_work writes the ghost stream work of the level's two sub-steps,
+ * {cells 1, values 1, cells 2, values 2}: the ghost-layer cells and (cell, direction) values
+ * that the stream computes because a later pull reads them (owned pulls of sub-step 2 read
+ * layer 1; the coalescence of Eq. ftoc reads the coalescing directions of the children), the
+ * rest of ghost layers 1-2 being never read (Sec. 4.3-4.4). */
 lbm_status lbm_plan_create(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag,
                            void* user, lbm_plan** out);
 lbm_status lbm_plan_num_levels(const lbm_plan* p, int32_t* n_levels);
 lbm_status lbm_plan_leaves(const lbm_plan* p, int32_t level, int32_t* n, int32_t* blocks);
 lbm_status lbm_plan_counts(const lbm_plan* p, int32_t level, int64_t counts[4]);
+lbm_status lbm_plan_ghost_work(const lbm_plan* p, int32_t level, int64_t work[4]);
 lbm_status lbm_plan_destroy(lbm_plan* p);
 
 /* ---- forest lifetime --------------------------------------------------------------------
@@ -156,8 +162,9 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
 
 /* Advances n_steps coarse time steps: Alg. 1 with same-level exchange, boundary treatment and
  * coalescence fused into each level's stream-collide kernel (Alg. 2), and one explosion kernel
- * per visit of a finer level.  The whole coarse step is one CUDA graph, replayed per step on
- * the forest's stream; asynchronous. */
+ * per visit of a finer level (Eq. ctof; it writes the ghost values that owned cells pull in the
+ * first sub-step, the stream reads the others from the coarse parents).  The whole coarse step
+ * is one CUDA graph, replayed per step on the forest's stream; asynchronous. */
 lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps);
 
 /* Macroscopic fields (Eq. fvelocity; the velocity adds a_L/2 as in Sec. 2.1) of the current
@@ -180,9 +187,10 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
 /* ---- measurement -------------------------------------------------------------------------
  * lbm_timing_begin(f, max_steps) makes the next lbm_step_coarse calls (at most max_steps
  * coarse steps in total) enqueue the step's kernels directly, with a CUDA event recorded on the
- * forest's stream before and after every kernel (the same launches the captured graph holds).  lbm_timing_end synchronises and returns, per level, the summed time in ms
- * and the number of launches of the stream-collide kernels and of the explosion kernels
- * (arrays of length n_levels; any may be NULL), then stops timing. */
+ * forest's stream before and after every kernel (the same launches the captured graph holds).
+ * lbm_timing_end synchronises and returns, per level, the summed time in ms and the number of
+ * launches of the stream-collide kernels and of the explosion kernels (arrays of length
+ * n_levels; any may be NULL), then stops timing. */
 lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);
 lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level,
                           double* ms_explode_per_level, int64_t* launches_explode_per_level);

@@ -5,11 +5,13 @@
 // levels).  Per coarse step, with F_L(s) the fused kernel of level L in its sub-step s and
 // E_L the explosion into level L's ghost layers:
 //     S(0) = [S(1)] F_0(1)      S(L) = E_L [S(L+1)] F_L(1) [S(L+1)] F_L(2)   (L >= 1)
-// E_L copies the coarse post-collision state into ghost layers 1-3 (Eq. ctof); F_L(1) carries
-// stream, coalescence (reads of the finer ghost layers) and the second collision of Alg. 1;
-// F_L(2) carries the second stream and the first collision of the next visit.  Levels >= 1
-// flip their two-grid parity an even number of times per coarse step, level 0 once; the
-// runtime therefore captures one graph per level-0 parity and replays them alternately.
+// E_L copies the coarse post-collision state into the ghost-layer-1 values that owned cells of
+// level L pull in sub-step 1 (Eq. ctof); the ghost stream reads the other exploded values it
+// needs from the coarse parents, which level L-1 leaves unchanged until S(L) returns.  F_L(1)
+// carries stream, coalescence (reads of the finer ghost layers) and the second collision of
+// Alg. 1; F_L(2) carries the second stream and the first collision of the next visit.  Levels >= 1 flip their two-grid parity an even number of times
+// per coarse step, level 0 once; the runtime therefore captures one graph per level-0 parity and
+// replays them alternately.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -55,14 +57,13 @@ struct Launch {
 struct DevBuf {
     void* f[2] = {nullptr, nullptr};
     uint8_t* cell = nullptr;
-    int32_t *nbr = nullptr, *parent = nullptr, *child = nullptr, *pos = nullptr, *gcells = nullptr;
+    int32_t *nbr = nullptr, *parent = nullptr, *child = nullptr, *pos = nullptr;
     uint8_t* kind = nullptr;
     uint32_t* link = nullptr;
-    uint32_t* glink = nullptr;
     uint32_t* colsolid = nullptr;
     uint8_t* colspec = nullptr;
-    int32_t* ecells = nullptr;
-    int32_t* eparent = nullptr;
+    uint32_t* gwork[2] = {nullptr, nullptr};
+    uint32_t* ework = nullptr;
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -178,12 +179,13 @@ void build_schedule(lbm_forest* f) {
         int lzc = f->lzc;
         while (lzc > 0 && int64_t(V.nown) * B * B * (B >> lzc) / 256 < int64_t(4) * sms * f->minb) lzc--;
         const int64_t units = int64_t(V.nown) * B * B * (B >> lzc);
-        int grid = int((units + 255) / 256) + int((V.gcells.size() + 255) / 256);
+        const int64_t nwork = int64_t(V.gwork[s - 1].size() / 4);
+        int grid = int((units + 255) / 256) + int((nwork + 255) / 256);
         f->sched.push_back({L, s, grid, 0, lzc});
     };
     auto explode = [&](int L) {
         const HostLevel& V = f->plan.lv[L];
-        f->sched.push_back({L, 0, int((V.ecells.size() + 255) / 256), 1, 0});
+        f->sched.push_back({L, 0, int((V.ework.size() / 4 + 255) / 256), 1, 0});
     };
     std::function<void(int)> rec = [&](int L) {
         if (L == 0) {
@@ -207,7 +209,7 @@ void enqueue_step(lbm_forest* f, cudaStream_t s, int* cur, cudaEvent_t* evs) {
         const Launch& l = f->sched[k];
         if (evs) cudaEventRecord(evs[k], s);
         if (l.type == 1) {
-            f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], f->plan.LB, s);
+            f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], s);
             continue;
         }
         StepArgs a = make_args(f, l, cur);
@@ -324,6 +326,20 @@ lbm_status lbm_plan_counts(const lbm_plan* p, int32_t level, int64_t counts[4]) 
     return LBM_OK;
 }
 
+lbm_status lbm_plan_ghost_work(const lbm_plan* p, int32_t level, int64_t work[4]) {
+    if (!p || !work) return fail(LBM_EINVAL, "NULL argument");
+    if (level < 0 || level >= p->p.nlev) return fail(LBM_EINVAL, "level out of range");
+    const HostLevel& V = p->p.lv[level];
+    for (int s = 0; s < 2; s++) {
+        const std::vector<uint32_t>& g = V.gwork[s];
+        int64_t values = 0;
+        for (size_t i = 0; i < g.size(); i += 4) values += __builtin_popcount(g[i + 1]);
+        work[2 * s] = int64_t(g.size() / 4);
+        work[2 * s + 1] = values;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_plan_destroy(lbm_plan* p) {
     delete p;
     return LBM_OK;
@@ -342,14 +358,13 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.parent);
         cudaFree(b.child);
         cudaFree(b.pos);
-        cudaFree(b.gcells);
         cudaFree(b.kind);
         cudaFree(b.link);
-        cudaFree(b.glink);
         cudaFree(b.colsolid);
         cudaFree(b.colspec);
-        cudaFree(b.ecells);
-        cudaFree(b.eparent);
+        cudaFree(b.gwork[0]);
+        cudaFree(b.gwork[1]);
+        cudaFree(b.ework);
     }
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
@@ -398,10 +413,10 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
                                  (long long)(ncells * Q * f->esize), L));
         lbm_status s;
         if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
-            (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.gcells, V.gcells)) ||
-            (s = upload(&b.kind, V.kind)) || (s = upload(&b.link, V.link)) || (s = upload(&b.glink, V.glink)) ||
-            (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.colspec, V.colspec)) || (s = upload(&b.ecells, V.ecells)) ||
-            (s = upload(&b.eparent, V.eparent)))
+            (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.kind, V.kind)) ||
+            (s = upload(&b.link, V.link)) || (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.colspec, V.colspec)) ||
+            (s = upload(&b.gwork[0], V.gwork[0])) || (s = upload(&b.gwork[1], V.gwork[1])) ||
+            (s = upload(&b.ework, V.ework)))
             return bail(s);
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -412,17 +427,17 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.child = b.child;
         g.pos = b.pos;
         g.kind = b.kind;
-        g.gcells = b.gcells;
         g.link = b.link;
-        g.glink = b.glink;
         g.colsolid = b.colsolid;
         g.colspec = b.colspec;
-        g.ecells = b.ecells;
-        g.eparent = b.eparent;
-        g.necells = int(V.ecells.size());
+        g.ework = reinterpret_cast<const uint4*>(b.ework);
+        g.nework = int(V.ework.size() / 4);
+        for (int k = 0; k < 2; k++) {
+            g.gwork[k] = reinterpret_cast<const uint4*>(b.gwork[k]);
+            g.ngwork[k] = int(V.gwork[k].size() / 4);
+        }
         g.nown = V.nown;
         g.nbricks = V.nbricks();
-        g.ngcells = int(V.gcells.size());
         g.ncells = ncells;
         for (int a = 0; a < 3; a++) g.N[a] = V.N[a];
         f->updates += V.nfluid << L;

@@ -5,13 +5,15 @@
 // and corners) differ by at most one level, every leaf holding B^3 cells.  On top of the
 // leaf set this file derives what the GPU kernels need per level:
 //  - owned bricks (the level's leaves) and ghost bricks: block positions covered by the
-//    next coarser level that touch an owned brick; they hold the fine ghost layers of
-//    Sec. 4 (layers 1-2 are streamed, layer 3 holds the exploded coarse value);
+//    next coarser level that touch an owned brick; they hold the fine ghost layers 1-2 of
+//    Sec. 4 (layer 3 is a source only, whose value is the coarse parent's);
 //  - a 27-entry neighbour table per brick (periodic axes wrap), parent links from ghost
 //    bricks to the coarse brick under them (explosion, Eq. ctof) and child links from owned
 //    bricks to the finer ghost bricks inside them (coalescence, Eq. ftoc);
 //  - a cell class per cell, with ghost cells taking the obstacle flag of the coarse cell that
-//    covers them, so fluid/obstacle marking agrees across the interface (Sec. 4.1).
+//    covers them, so fluid/obstacle marking agrees across the interface (Sec. 4.1);
+//  - per owned cell the links that are not plain loads, in each sub-step, and per sub-step the
+//    list of ghost values that some later pull reads (see ghost_work).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -273,34 +275,62 @@ struct Builder {
         return true;
     }
 
-    // Link bits of cell (x, y, z) of brick k: bit q is set when pull q is not a plain load of a
-    // stored value of this level (the source is an obstacle or lies beyond a wall, or, for owned
-    // cells, coalescence replaces the PDF).  With the explosion written into ghost layers 1-3 by
-    // the coarser level, sources in ghost layers are stored values.
-    uint32_t link_bits(const HostLevel& V, int k, int x, int y, int z, bool owned) const {
+    // Source of pull q into cell (x, y, z) of brick k: its brick (or an NB_* code) and, for a
+    // brick, the cell index in the level's grid.
+    void source(const HostLevel& V, int k, int x, int y, int z, int q, int32_t& nb, int64_t& cell) const {
         const int B = p.B, B3 = B * B * B, M = B - 1;
+        const int s[3] = {x - EX[q], y - EY[q], z - EZ[q]};
+        int o[3];
+        for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
+        nb = (o[0] | o[1] | o[2]) ? V.nbr[size_t(k) * 27 + 13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
+        cell = nb >= 0 ? int64_t(nb) * B3 + (int64_t(s[2] & M) * B + (s[1] & M)) * B + (s[0] & M) : -1;
+    }
+
+    // Coalescence links of owned fluid cell (x, y, z) of brick k (Eq. ftoc): bit q is set when
+    // the upwind cell along e_q, or along one axis component of e_q, lies in the finer level.
+    uint32_t coal_bits(const HostLevel& V, int k, int x, int y, int z) const {
+        if (!(V.kind[k] & BK_TOUCH_FINER)) return 0;
+        const int M = p.B - 1;
         const int32_t* nbr = &V.nbr[size_t(k) * 27];
-        const bool finer = owned && (V.kind[k] & BK_TOUCH_FINER);
         uint32_t m = 0;
         for (int q = 1; q < Q; q++) {
             int s[3] = {x - EX[q], y - EY[q], z - EZ[q]}, o[3];
             for (int a = 0; a < 3; a++) o[a] = s[a] < 0 ? -1 : (s[a] > M ? 1 : 0);
-            int32_t nb = (o[0] | o[1] | o[2]) ? nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
-            bool plain = false;
-            if (nb >= 0) {
-                uint8_t ck = V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)];
-                plain = ck == CK_FLUID || ck == CK_GHOST || ck == CK_G3;
-            }
-            if (finer) {
-                bool coal = nb == NB_FINER;
-                if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
-                if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
-                if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
-                if (coal) plain = false;
-            }
+            bool coal = (o[0] | o[1] | o[2]) && nbr[13 + o[0] + 3 * o[1] + 9 * o[2]] == NB_FINER;
+            if (EX[q] && o[0] && nbr[13 + o[0]] == NB_FINER) coal = true;
+            if (EY[q] && o[1] && nbr[13 + 3 * o[1]] == NB_FINER) coal = true;
+            if (EZ[q] && o[2] && nbr[13 + 9 * o[2]] == NB_FINER) coal = true;
+            if (coal) m |= 1u << q;
+        }
+        return m;
+    }
+
+    // Link bits of cell (x, y, z) of brick k: bit q is set when pull q is not a plain load of a
+    // stored value of this level (the source is an obstacle or lies beyond a wall, or, for owned
+    // cells, coalescence replaces the PDF).  Sources in ghost layers 1-3 count as plain here.
+    uint32_t link_bits(const HostLevel& V, int k, int x, int y, int z, bool owned) const {
+        uint32_t m = owned ? coal_bits(V, k, x, y, z) : 0u;
+        for (int q = 1; q < Q; q++) {
+            int32_t nb;
+            int64_t c;
+            source(V, k, x, y, z, q, nb, c);
+            const bool plain = nb >= 0 && (V.cell[c] == CK_FLUID || V.cell[c] == CK_GHOST || V.cell[c] == CK_G3);
             if (!plain) m |= 1u << q;
         }
         return m;
+    }
+
+    // Plain links of an owned cell (not in m) whose source lies in a ghost brick.
+    uint32_t ghost_src_bits(const HostLevel& V, int k, int x, int y, int z, uint32_t m) const {
+        uint32_t g = 0;
+        for (int q = 1; q < Q; q++) {
+            if ((m >> q) & 1u) continue;
+            int32_t nb;
+            int64_t c;
+            source(V, k, x, y, z, q, nb, c);
+            if (nb >= V.nown) g |= 1u << q;
+        }
+        return g;
     }
 
     // Wall face whose boundary condition a source beyond the domain takes: the first face it
@@ -361,8 +391,7 @@ struct Builder {
     }
 
     // Owned cells: link bits and bit 31 for non-fluid cells; per owned column the bitmap of its
-    // non-fluid cells and whether any of its cells has a nonzero link mask.  Ghost bricks: the
-    // stream and explosion work lists.
+    // non-fluid cells and whether any of its cells has a nonzero link mask.
     void links(int L) {
         HostLevel& V = p.lv[L];
         const int B = p.B, B3 = B * B * B;
@@ -391,26 +420,115 @@ struct Builder {
                         V.link[c] = m;
                         if (m) V.colspec[size_t(k) * B * B + size_t(y) * B + x] = 1;
                     }
-        // ghost work lists in cell order: the ghost-layer-1/2 fluid cells (stream) and the fluid
-        // cells of layers 1-3 (explosion targets)
-        for (int k = V.nown; k < V.nbricks(); k++)
+    }
+
+    // Explosion and ghost stream work of level L (Sec. 4.3-4.4).  The fine level reads ghost
+    // values in four places: the owned pulls of sub-step 1 read layer 1 as exploded (Eq. ctof);
+    // the owned pulls of sub-step 2 read layer 1 after its sub-step-1 stream; the coalescence of
+    // the coarser level reads the children of each coalescing coarse cell after the sub-step-2
+    // stream, in the coalescing directions only (Eq. ftoc); and each streamed value depends on the
+    // value of its source one sub-step earlier (or, for a bounce-back, on the cell's own opposite
+    // value).  Every other ghost value is never read, so the explosion writes and the stream
+    // computes exactly this set.  A stream source in the ghost layers before sub-step 1, or in
+    // layer 3 at any time, holds the exploded value, which the stream reads from the coarse parent.
+    bool ghost_work(int L, std::string& err) {
+        HostLevel& V = p.lv[L];
+        if (L == 0 || V.nghost == 0) return true;
+        const HostLevel& C = p.lv[L - 1];
+        const int B = p.B, B3 = B * B * B, M = B - 1, LB = p.LB;
+        const int64_t g0 = int64_t(V.nown) * B3, ng = int64_t(V.nghost) * B3;
+        std::vector<uint32_t> need[2], coarse[2], special[2];
+        for (int s = 0; s < 2; s++) {
+            need[s].assign(size_t(ng), 0u);
+            coarse[s].assign(size_t(ng), 0u);
+            special[s].assign(size_t(ng), 0u);
+        }
+        // after sub-step 2: the children of coalescing coarse cells (Eq. ftoc)
+        for (int kc = 0; kc < C.nown; kc++) {
+            if (!(C.kind[kc] & BK_TOUCH_FINER)) continue;
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
                     for (int x = 0; x < B; x++) {
-                        const int c = int(size_t(k) * B3 + (size_t(z) * B + y) * B + x);
-                        const uint8_t ck = V.cell[c];
-                        if (ck == CK_GHOST) {
-                            V.gcells.push_back(c);
-                            V.glink.push_back(link_bits(V, k, x, y, z, false));
+                        if (C.cell[size_t(kc) * B3 + (size_t(z) * B + y) * B + x] != CK_FLUID) continue;
+                        const uint32_t cm = coal_bits(C, kc, x, y, z);
+                        if (!cm) continue;
+                        const int oct = ((2 * x) >> LB) | (((2 * y) >> LB) << 1) | (((2 * z) >> LB) << 2);
+                        const int cb = C.child[size_t(kc) * 8 + oct];
+                        if (cb < V.nown) {
+                            err = "coalescing cell without a finer ghost brick";
+                            return false;
                         }
-                        if (ck == CK_GHOST || ck == CK_G3) {
-                            V.ecells.push_back(ck == CK_G3 ? int32_t(uint32_t(c) | (1u << 31)) : c);
-                            const int pk = V.parent[k], pb = pk >> 3, oct = pk & 7;
-                            const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1;
-                            const int pz = ((oct >> 2) * B + z) >> 1;
-                            V.eparent.push_back(int32_t(size_t(pb) * B3 + (size_t(pz) * B + py) * B + px));
+                        for (int d = 0; d < 8; d++) {
+                            const int cx = (2 * x & M) + (d & 1), cy = (2 * y & M) + ((d >> 1) & 1), cz = (2 * z & M) + (d >> 2);
+                            const int64_t c = int64_t(cb) * B3 + (int64_t(cz) * B + cy) * B + cx;
+                            if (V.cell[c] != CK_GHOST) {
+                                err = "a coalescence child lies outside ghost layers 1-2";
+                                return false;
+                            }
+                            need[1][c - g0] |= cm;
                         }
                     }
+        }
+        // after sub-step 1: the layer-1 values that owned cells pull in sub-step 2
+        for (int k = 0; k < V.nown; k++)
+            for (int z = 0; z < B; z++)
+                for (int y = 0; y < B; y++)
+                    for (int x = 0; x < B; x++) {
+                        const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
+                        if (V.cell[c] != CK_FLUID) continue;
+                        const uint32_t gq = ghost_src_bits(V, k, x, y, z, V.link[c] & 0x7FFFEu);
+                        for (int q = 1; q < Q; q++) {
+                            if (!((gq >> q) & 1u)) continue;
+                            int32_t nb;
+                            int64_t sc;
+                            source(V, k, x, y, z, q, nb, sc);
+                            if (V.cell[sc] != CK_GHOST) {
+                                err = "an owned cell pulls from beyond ghost layer 1";
+                                return false;
+                            }
+                            need[0][sc - g0] |= 1u << q;
+                        }
+                    }
+        // the explosion writes these same layer-1 values before sub-step 1
+        for (int64_t i = 0; i < ng; i++) {
+            if (!need[0][i]) continue;
+            const int k = int((g0 + i) / B3), l = int((g0 + i) % B3);
+            const int x = l & M, y = (l >> LB) & M, z = l >> (2 * LB);
+            const int pk = V.parent[k], pb = pk >> 3, oct = pk & 7;
+            const int px = ((oct & 1) * B + x) >> 1, py = (((oct >> 1) & 1) * B + y) >> 1, pz = ((oct >> 2) * B + z) >> 1;
+            const int64_t pc = int64_t(pb) * B3 + (int64_t(pz) * B + py) * B + px;
+            V.ework.insert(V.ework.end(), {uint32_t(g0 + i), need[0][i], uint32_t(pc), 0u});
+        }
+        // sources of every needed value, sub-step 2 first (it adds sub-step-1 needs)
+        for (int s = 1; s >= 0; s--)
+            for (int64_t i = 0; i < ng; i++) {
+                if (!need[s][i]) continue;
+                const int k = int((g0 + i) / B3), l = int((g0 + i) % B3);
+                const int x = l & M, y = (l >> LB) & M, z = l >> (2 * LB);
+                const uint32_t gl = link_bits(V, k, x, y, z, false);
+                for (int q = 1; q < Q; q++) {
+                    if (!((need[s][i] >> q) & 1u)) continue;
+                    int32_t nb;
+                    int64_t sc;
+                    source(V, k, x, y, z, q, nb, sc);
+                    if ((gl >> q) & 1u) {
+                        const bool bounce = nb == NB_WALL || (nb >= 0 && V.cell[sc] == CK_SOLID);
+                        if (!bounce) {
+                            err = "a needed ghost value has no source within ghost layer 3";
+                            return false;
+                        }
+                        special[s][i] |= 1u << q;
+                        if (s == 1) need[0][i] |= 1u << OPP[q];
+                    } else if (nb >= V.nown) {
+                        if (s == 0 || V.cell[sc] == CK_G3) coarse[s][i] |= 1u << q;
+                        else need[0][sc - g0] |= 1u << q;
+                    }
+                }
+            }
+        for (int s = 0; s < 2; s++)
+            for (int64_t i = 0; i < ng; i++)
+                if (need[s][i]) V.gwork[s].insert(V.gwork[s].end(), {uint32_t(g0 + i), need[s][i], coarse[s][i], special[s][i]});
+        return true;
     }
 
     void children(int L) {
@@ -499,6 +617,8 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
         }
         b.links(L);
     }
+    for (int L = 1; L < p.nlev; L++)
+        if (!b.ghost_work(L, err)) return false;
     return true;
 }
 

@@ -26,16 +26,15 @@ struct DevLevel {
     const int32_t* child;
     const int32_t* pos;   // [nbricks][3]
     const uint8_t* kind;  // [nbricks]
-    const int32_t* gcells;
-    const uint32_t* link; // [nown * B^3] per owned cell: bit q set = link q needs the general pull;
-                          // bits 29-30 = explosion code; bit 31 = the cell is not a fluid cell
-    const uint32_t* glink;  // [ngcells] link bits of the ghost work list
+    const uint32_t* link;    // [nown * B^3] per owned cell: bit q set = link q needs the general
+                             // pull; bits 25-29 fast-path codes; bit 31 = not a fluid cell
     const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
     const uint8_t* colspec;    // [nown * B^2] per owned column: 1 if any cell has a nonzero link mask
-    const int32_t* ecells;     // explosion targets; bit 31 = ghost layer 3
-    const int32_t* eparent;    // coarse parent cell of each explosion target
-    int necells;
-    int nown, nbricks, ngcells;
+    const uint4* gwork[2];     // ghost stream work of sub-step 1 and 2: {cell, need, coarse, special}
+    int ngwork[2];
+    const uint4* ework;        // explosion work: {cell, directions, coarse parent cell, 0}
+    int nework;
+    int nown, nbricks;
     int64_t ncells;
     int N[3];
 };
@@ -43,7 +42,8 @@ struct DevLevel {
 struct StepArgs {
     DevLevel lv, co, fi;  // this level, the next coarser, the next finer
     int cur, cur_c, cur_f;
-    int substep;          // 1: ghost layers hold exploded values; 2: they hold sub-step-1 values
+    int substep;          // 1: ghost layers hold the exploded (coarse) values; 2: layers 1-2 hold
+                          // their sub-step-1 stream
     int LB;
     int lzc;              // log2 of the cells each thread walks along z
     int minb;             // CTAs per SM the kernel variant is compiled for (2, 3 or 4)
@@ -70,7 +70,7 @@ struct Launchers {
     void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
                    int grid, cudaStream_t s);
-    void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int LB, cudaStream_t s);
+    void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s);
 };
 const Launchers& launchers_f64();
 const Launchers& launchers_f32();

@@ -52,10 +52,9 @@ struct LaunchImpl {
         if (grid <= 0) return;
         reduce_level_kernel<T><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, w, partial);
     }
-    static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int LB, cudaStream_t s) {
-        if (lv.necells <= 0) return;
-        (void)LB;
-        explode_kernel<T><<<dim3((lv.necells + 255) / 256, 19), 256, 0, s>>>(lv, co, cur, cur_c);
+    static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s) {
+        if (lv.nework <= 0) return;
+        explode_kernel<T><<<(lv.nework + 255) / 256, 256, 0, s>>>(lv, co, cur, cur_c);
     }
     static const Launchers& get() {
         static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode};

@@ -22,7 +22,7 @@ enum : uint8_t {
     CK_GHOST = 1,  // fluid cell of ghost layers 1-2 (covered by the coarser level): streams only
     CK_FAR = 2,    // fluid cell of ghost layer 4 or beyond: never read
     CK_SOLID = 3,  // no-slip obstacle
-    CK_G3 = 4,     // fluid cell of ghost layer 3: holds the exploded coarse value, never streamed
+    CK_G3 = 4,     // fluid cell of ghost layer 3: its value is the coarse parent's, never stored
 };
 // Neighbour-table codes for block positions that hold no brick of this level.
 enum : int32_t { NB_WALL = -1, NB_FINER = -2, NB_COARSE = -3 };
@@ -41,17 +41,19 @@ struct HostLevel {
     std::vector<int32_t> child;    // [nown][8] ghost brick of L+1 under each octant, or -1
     std::vector<uint8_t> kind;     // [nbricks] BK_* bits
     std::vector<uint8_t> cell;     // [nbricks * B^3] CK_* per cell
-    std::vector<int32_t> gcells;   // ghost stream work list: the fluid cells of ghost layers 1-2
-    std::vector<uint32_t> glink;   // [gcells] link bits
-    std::vector<int32_t> ecells;   // explosion targets: the fluid cells of ghost layers 1-3;
-                                   // bit 31 = layer 3
-    std::vector<int32_t> eparent;  // [ecells] the coarse parent cell of each target on level L-1
     std::vector<uint32_t> link;    // [nown * B^3] per owned cell: bit q = link q is not a plain
                                    // same-level load; bit 29 = every such link is a bounce-back
                                    // (bits 25-27: wall face of its wall term, 7 = none); bit 28 =
                                    // every such link is a coalescence link; bit 31 = not fluid
     std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
     std::vector<uint8_t> colspec;    // [nown * B^2] 1 if any cell of the column has a nonzero link mask
+    // Ghost stream work of sub-step s+1: 4 words per entry {cell, need, coarse, special}: the
+    // directions of the cell whose value a later pull reads, those whose source value is the
+    // coarse parent's, and those that are not plain loads (bounce-back, wall).
+    std::vector<uint32_t> gwork[2];
+    // Explosion work: 4 words per entry {cell, directions, coarse parent cell, 0}: the ghost-layer-1
+    // values that owned cells pull in sub-step 1, copied from the parent (Eq. ctof).
+    std::vector<uint32_t> ework;
     int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }

@@ -3,8 +3,11 @@
 //
 // Storage per level: two PDF grids (Sec. 4.1 two-grid approach), each [19][ncells] with the
 // cells of brick k at [k * B^3, (k+1) * B^3), x fastest.  The grids hold the POST-COLLISION
-// state of owned cells (f-tilde, stored by the fused kernel) and the streamed values of ghost
-// layers 1-2.  FP32/FP16 storage holds f - w rho0 ("shifted"); FP64 holds f.
+// state of owned cells (f-tilde, stored by the fused kernel) and the ghost-layer values that a
+// later pull reads: the exploded layer-1 values that owned cells pull in sub-step 1 (Eq. ctof:
+// every ghost cell takes its coarse parent's post-collision PDFs) and the streamed values of
+// layers 1-2.  The ghost stream reads the other exploded values it needs from the coarse parent
+// in the coarser level's grid.  FP32/FP16 storage holds f - w rho0 ("shifted"); FP64 holds f.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -135,6 +138,16 @@ struct Access {
     __device__ __forceinline__ C load(const void* base, int64_t n, int q, int64_t idx) const {
         return C(Store<T>::ld(static_cast<const T*>(base) + int64_t(q) * n + idx));
     }
+    // Exploded value of direction q in cell (lx, ly, lz) of ghost brick gb (Eq. ctof): the
+    // post-collision PDF of the coarse parent cell, which the coarser level's current grid holds
+    // unchanged while this level runs its two sub-steps.
+    __device__ __forceinline__ C coarse(int gb, int lx, int ly, int lz, int q) const {
+        const int P = __ldg(a.lv.parent + gb);
+        const int cb = P >> 3, oct = P & 7, H = 1 << (LB - 1);
+        const int cx = (oct & 1) * H + (lx >> 1), cy = ((oct >> 1) & 1) * H + (ly >> 1), cz = (oct >> 2) * H + (lz >> 1);
+        const int64_t idx = (int64_t(cb) << (3 * LB)) + (cz << (2 * LB)) + (cy << LB) + cx;
+        return load(a.co.f[a.cur_c], a.co.ncells, q, idx);
+    }
     // Mean of the 8 finer children of owned cell (x, y, z) of brick b after both fine sub-steps
     // (coalescence, Eq. ftoc), summed pairwise in z-y-x bit order.  With FP64 storage the sum is
     // FP64.  With FP32/FP16 storage it is an FP32 double-word sum (Knuth's TwoSum at every
@@ -187,9 +200,9 @@ template <> struct Par<float> {
 //   - coalescence (owned cells only): mean of the 8 finer children of x (Eq. ftoc);
 //   - obstacle or domain wall: bounce-back of the cell's own opposite value (Sec. 2.2), plus
 //     6 w rho0 e.u_w on velocity walls; a source beyond several faces takes the first of
-//     z+, z-, y+, y-, x+, x-;
-//   - otherwise the stored value of the source cell (owned, or ghost layers 1-3, which hold the
-//     exploded coarse values or their first-sub-step stream).
+//     z+, z-, y+, y-, x+, x-.  A ghost cell's own value in sub-step 1 is the exploded one;
+//   - otherwise the value of the source cell: stored (owned, or ghost layers 1-2 after their
+//     sub-step-1 stream), or exploded (ghost layers in sub-step 1, layer 3 always).
 template <typename T, typename C, int LB>
 __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick, int x, int y, int z, int q,
                           bool owned) {
@@ -212,11 +225,13 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
         if (coal) return acc.children_mean(brick, x, y, z, q);
     }
     const int qo = dopp(q);
+    const bool own_exploded = !owned && a.substep == 1;
     if (nb >= 0) {
         const int64_t sidx = (int64_t(nb) << B3s) + ((sz & M) << (2 * LB)) + ((sy & M) << LB) + (sx & M);
         const uint8_t ck = __ldg(a.lv.cell + sidx);
-        if (ck == CK_SOLID) return acc.load(src, n, qo, cidx);
+        if (ck == CK_SOLID) return own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
         if (ck == CK_FAR) return qnan<C>();   // never a source: layer 4+ holds no value
+        if (nb >= a.lv.nown && (a.substep == 1 || ck == CK_G3)) return acc.coarse(nb, sx & M, sy & M, sz & M, q);
         return acc.load(src, n, q, sidx);
     }
     if (nb == NB_WALL) {
@@ -229,18 +244,19 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
         else if (!(a.per & 2) && gy < 0) face = 2;
         else if (!(a.per & 1) && gx >= a.lv.N[0]) face = 1;
         else face = 0;
-        return acc.load(src, n, qo, cidx) + C(__ldg(a.wall + face * 19 + q));
+        const C o = own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
+        return o + C(__ldg(a.wall + face * 19 + q));
     }
     return qnan<C>();
 }
 
 // One sub-step of one level (Alg. 2 StreamCollide generalised to every level): pull stream with
 // boundary treatment and coalescence, then collide owned cells; ghost layers 1-2 are streamed
-// only (their sources were filled by explode_kernel).  Owned cells: each thread walks 2^lzc cells
-// of one (x, y) column of a brick; the source offsets of a cell inside the brick are computed once
+// only, and only the values a later pull reads.  Owned cells: each thread walks 2^lzc cells of
+// one (x, y) column of a brick; the source offsets of a cell inside the brick are computed once
 // per column, obstacle cells are skipped by a per-column bitmap, and a per-cell link mask (read
 // where the brick needs it) routes the few links that are not plain loads to pull_general.  CTAs
-// after the owned part cover the ghost work list.
+// after the owned part cover the ghost work list of this sub-step.
 template <typename T, typename C, int COLL, int LB, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
@@ -383,62 +399,65 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
         }
         return;
     }
-    // ghost layers 1-2: stream only; sources are stored values except where the link mask says
+    // ghost layers 1-2: stream only, the directions the work entry needs; a source holding an
+    // exploded value is read from the coarse parent, and bounce-back/wall links take the general pull
+    const int gs = a.substep - 1;
     const int i = int(int64_t(blockIdx.x - owned_ctas) * 256 + tid);
-    if (i >= a.lv.ngcells) return;
-    const int c = __ldg(a.lv.gcells + i);
+    if (i >= a.lv.ngwork[gs]) return;
+    const uint4 e = __ldg(a.lv.gwork[gs] + i);
+    const int c = int(e.x);
+    const uint32_t need = e.y, cm = e.z, sm = e.w;
     const int brick = c >> B3s, local = c & ((1 << B3s) - 1);
     const int x = local & M, y = (local >> LB) & M, z = local >> B2s;
     const int* nbr = a.lv.nbr + brick * 27;
     C v[19];
-    {
-        const T* p = src;
-        v[0] = C(Store<T>::ld(p + c));
 #pragma unroll
-        for (int q = 1; q < 19; q++) {
-            p += n;
+    for (int q = 1; q < 19; q++) {
+        v[q] = C(0);
+        if (((need & ~sm) >> q) & 1u) {
             const int sx = x - dex(q), sy = y - dey(q), sz = z - dez(q);
             const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
             const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
             const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
             const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
-            const int sidx = (max(nb, 0) << B3s) + ((sz & M) << B2s) + ((sy & M) << LB) + (sx & M);
-            v[q] = C(Store<T>::ld(p + sidx));
+            if ((cm >> q) & 1u) {
+                v[q] = acc.coarse(nb, sx & M, sy & M, sz & M, q);
+            } else {
+                const int sidx = (max(nb, 0) << B3s) + ((sz & M) << B2s) + ((sy & M) << LB) + (sx & M);
+                v[q] = acc.load(src, n, q, sidx);
+            }
         }
     }
-    const uint32_t mq = __ldg(a.lv.glink + i) & LINK_ALL;
-    if (mq) {
+    if (sm) {
         for (int q = 1; q < 19; q++)
-            if ((mq >> q) & 1u) slow[0][q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
+            if ((sm >> q) & 1u) slow[0][q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, false);
 #pragma unroll
         for (int q = 1; q < 19; q++)
-            if ((mq >> q) & 1u) v[q] = slow[0][q][tid];
+            if ((sm >> q) & 1u) v[q] = slow[0][q][tid];
     }
     T* p = dst + c;
 #pragma unroll
-    for (int q = 0; q < 19; q++) {
-        Store<T>::st(p, v[q]);
-        p += n;
-    }
+    for (int q = 1; q < 19; q++)
+        if ((need >> q) & 1u) Store<T>::st(p + int64_t(q) * n, v[q]);
 }
 
-// Explosion (Eq. ctof): at the start of every visit of a finer level, each cell of its
-// explosion list takes all 19 values of its coarse parent's post-collision state, in the finer
-// level's current grid; cells of ghost layer 3 (never streamed, read by layer 2) also in the other
-// grid, which the second sub-step reads.  Layer 4 is never read and is not written.  The list
-// holds the parent index of each entry; blockIdx.y is the direction, so every thread moves one
-// value.
+// Explosion (Eq. ctof) at the start of every visit of a finer level: the ghost-layer-1 values
+// that owned cells pull in sub-step 1 take their coarse parent's post-collision PDFs, in the finer
+// level's current grid.  One thread per work entry, one predicated copy per direction it lists.
 template <typename T>
 __global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= lv.necells) return;
-    const int q = blockIdx.y;
-    const uint32_t e = uint32_t(__ldg(lv.ecells + i));
-    const int c = int(e & 0x7FFFFFFFu);
-    const int pidx = __ldg(lv.eparent + i);
-    const T v = static_cast<const T*>(co.f[cur_c])[int64_t(q) * co.ncells + pidx];
-    static_cast<T*>(lv.f[cur])[int64_t(q) * lv.ncells + c] = v;
-    if (e >> 31) static_cast<T*>(lv.f[cur ^ 1])[int64_t(q) * lv.ncells + c] = v;
+    if (i >= lv.nework) return;
+    const uint4 e = __ldg(lv.ework + i);
+    const T* src = static_cast<const T*>(co.f[cur_c]) + e.z;
+    T* dst = static_cast<T*>(lv.f[cur]) + e.x;
+    T v[19];
+#pragma unroll
+    for (int q = 1; q < 19; q++)
+        if ((e.y >> q) & 1u) v[q] = __ldg(src + int64_t(q) * co.ncells);
+#pragma unroll
+    for (int q = 1; q < 19; q++)
+        if ((e.y >> q) & 1u) dst[int64_t(q) * lv.ncells] = v[q];
 }
 
 // Equilibrium start (Eq. fequ) followed by one collision, so the stored state is post-collision.

@@ -23,7 +23,7 @@ _COLL = {"srt": 0, "trt": 1}
 # Every entry point of include/lbm_gb300.h (checked by the tests).
 EXPORTS = [
     "lbm_last_error", "lbm_lattice", "lbm_plan_create", "lbm_plan_num_levels", "lbm_plan_leaves",
-    "lbm_plan_counts", "lbm_plan_destroy", "lbm_create_forest", "lbm_destroy", "lbm_num_levels",
+    "lbm_plan_counts", "lbm_plan_ghost_work", "lbm_plan_destroy", "lbm_create_forest", "lbm_destroy", "lbm_num_levels",
     "lbm_get_block_table", "lbm_cell_updates_per_coarse_step", "lbm_set_level_params",
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
@@ -81,6 +81,7 @@ def library():
             "lbm_plan_num_levels": [P, i32p],
             "lbm_plan_leaves": [P, ctypes.c_int32, i32p, i32p],
             "lbm_plan_counts": [P, ctypes.c_int32, i64p],
+            "lbm_plan_ghost_work": [P, ctypes.c_int32, i64p],
             "lbm_plan_destroy": [P],
             "lbm_create_forest": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, P, ctypes.POINTER(P)],
             "lbm_destroy": [P],
@@ -221,6 +222,12 @@ class Plan:
         c = np.zeros(4, np.int64)
         _check(library().lbm_plan_counts(self.h, level, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return dict(blocks=int(c[0]), fluid=int(c[1]), ghost12=int(c[2]), ghost_blocks=int(c[3]))
+
+    def ghost_work(self, level):
+        """Ghost stream work of the level's sub-steps: cells and (cell, direction) values."""
+        c = np.zeros(4, np.int64)
+        _check(library().lbm_plan_ghost_work(self.h, level, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return dict(cells1=int(c[0]), values1=int(c[1]), cells2=int(c[2]), values2=int(c[3]))
 
 
 class Forest:
