@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--no-variants", action="store_true", help="skip the FP64/FP16 side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched small-forest leg")
     return p.parse_args()
 
 
@@ -273,6 +274,56 @@ def _uniform(case):
     return inputs.uniform_field(u=case["u_init"])
 
 
+def _batch(lbm, torch, steps=500, warmup=5, serial_steps=50):
+    """The batched workload: 256 small lid-driven cavities (2-3 levels, 16^3 blocks, 8-64 leaves
+    each) stepped together, one launch per phase, after autotuning the batch's thread mapping;
+    beside it the same members stepped one forest after another."""
+    from paper_1508_07982_gb300 import inputs
+    cases = inputs.batch_cases()
+    fs = []
+    for c in cases:
+        f = lbm.Forest(c, precision="fp32s")
+        f.init_uniform()
+        fs.append(f)
+    b = lbm.Batch(fs)
+    lzc, minb, _ = b.autotune(4)
+    b.step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    upd = b.cell_updates_per_coarse_step()
+    launches = b.launches_per_coarse_step()
+    for f in fs:
+        f.step_coarse(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(serial_steps):
+        for f in fs:
+            f.step_coarse(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial = e0.elapsed_time(e1)
+    cells = sum(c["leaves"] for c in cases) * 16 ** 3
+    out = {"workload": "256 lid-driven cavities, 2-3 levels, 16^3 blocks, 8-64 leaves each (%d leaves, %.1fM cells)"
+                       % (sum(c["leaves"] for c in cases), cells / 1e6),
+           "value": round(upd * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT, "precision": "fp32s",
+           "steps": steps, "warmup": warmup, "ms_per_step": round(ms / steps, 5),
+           "cell_updates_per_coarse_step": int(upd), "gpu_launches_per_coarse_step": int(launches),
+           "kernel_config": {"cells_per_thread_log2": lzc, "ctas_per_sm": minb},
+           "one_forest_at_a_time": {"value": round(upd * serial_steps / (ms_serial / 1e3) / 1e9, 4), "unit": UNIT,
+                                    "ms_per_step": round(ms_serial / serial_steps, 5), "steps": serial_steps}}
+    b.close()
+    for f in fs:
+        f.close()
+    return out
+
+
 def run_reference(args, case):
     """The plain CPU oracle as the reference arm: each timed step is one full coarse step."""
     from oracle import oracle
@@ -372,6 +423,7 @@ def main():
             ref64.close()
 
     e2e = _e2e(lbm, torch, case, args.precision, min(args.steps, 200)) if rank == 0 and not args.no_e2e else None
+    batch = _batch(lbm, torch) if rank == 0 and not args.no_batch else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(case)
@@ -383,6 +435,8 @@ def main():
             "gpu_launches": int(launches * args.steps), "mass_total": mass[0]}
     if variants:
         line["precisions"] = variants
+    if batch:
+        line["batch"] = batch
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()

@@ -205,6 +205,44 @@ lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_
 /* Number of kernel launches one coarse step issues (the nodes of the captured graph). */
 lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n);
 
+/* Picks the fastest thread mapping for this forest: times n_steps coarse steps (Alg. 1) for every
+ * (cells_per_thread_log2 <= log2 B, ctas_per_sm in 2..4) pair, applies the fastest as
+ * lbm_set_kernel_config would, and writes it and its ms per coarse step (outputs may be NULL).
+ * The state of the forest (every level's two PDF grids and parities) is copied on the device first
+ * and restored afterwards, so the call leaves the simulation where it was; the copy needs as much
+ * device memory again as the PDF grids.  The results of later steps do not depend on the mapping.
+ * Synchronises the stream.  LBM_EINVAL if the forest is not initialised or is being timed. */
+lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
+                        double* ms_per_step);
+
+/* ---- batches of forests --------------------------------------------------------------------
+ * Many independent forests (for example a parameter study of small cases) stepped together:
+ * one coarse step of every member is Alg. 1 over the deepest member, and each phase of it (the
+ * stream-collide sub-step F_L(s) or the explosion E_L of one level, Sec. 4) is a single
+ * persistent launch over the work of all members, so that a phase of small forests fills the
+ * GPU with one launch instead of one per member.  Members without level L have no work in the
+ * phases of level L.  Each member computes exactly what lbm_step_coarse computes for it.
+ *
+ * lbm_batch_create(forests, n, out): the members must share precision, collision model, block
+ * size and stream; they stay owned by the caller, stay usable through every lbm_* call, and must
+ * outlive the batch.  The batch reads each member's buffers through pointers taken when it builds
+ * its graphs, so it must be destroyed and re-created after a member is re-created.
+ * lbm_batch_step(b, n): n coarse steps of every member on the members' stream (graph replay,
+ * asynchronous); every member must be initialised, with parameters set, and at the same two-grid
+ * parity (members stepped only together are).  lbm_batch_set_kernel_config / lbm_batch_autotune
+ * set or tune the thread mapping of the batch's launches as the single-forest calls do (autotune
+ * restores every member's state).  lbm_batch_cell_updates_per_coarse_step sums the members' cell
+ * updates; lbm_batch_launches_per_coarse_step counts the launches of one coarse step. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n_steps);
+lbm_status lbm_batch_set_kernel_config(lbm_batch* b, int32_t cells_per_thread_log2, int32_t ctas_per_sm);
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
+                              double* ms_per_step);
+lbm_status lbm_batch_cell_updates_per_coarse_step(const lbm_batch* b, int64_t* n);
+lbm_status lbm_batch_launches_per_coarse_step(const lbm_batch* b, int32_t* n);
+lbm_status lbm_batch_destroy(lbm_batch* b);
+
 /* ---- totals without allocation ------------------------------------------------------------
  * The paper has no counterpart: this entry point serves callers that cannot allocate device
  * memory when they need mass and momentum totals (code running during CUDA stream capture,

@@ -739,3 +739,379 @@ lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ kernel-config autotuning
+namespace {
+
+// Device copy of every level's two PDF grids and the parities, so that tuning runs leave the
+// state as they found it.
+struct Snapshot {
+    std::vector<void*> bufs;
+    std::vector<std::vector<int>> cur;
+};
+
+lbm_status take_snapshot(const std::vector<lbm_forest*>& fs, cudaStream_t s, Snapshot& sn) {
+    for (lbm_forest* f : fs) {
+        sn.cur.emplace_back(f->cur, f->cur + LBM_MAX_LEVELS);
+        for (int L = 0; L < f->plan.nlev; L++) {
+            const size_t bytes = size_t(f->dl[L].ncells) * Q * f->esize;
+            for (int k = 0; k < 2; k++) {
+                void* p = nullptr;
+                if (bytes) {
+                    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+                        sn.bufs.push_back(nullptr);
+                        return fail(LBM_ENOMEM, "cannot allocate the autotuning snapshot");
+                    }
+                    CU(cudaMemcpyAsync(p, f->dl[L].f[k], bytes, cudaMemcpyDeviceToDevice, s));
+                }
+                sn.bufs.push_back(p);
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status restore_snapshot(const std::vector<lbm_forest*>& fs, cudaStream_t s, Snapshot& sn) {
+    size_t k = 0;
+    for (size_t i = 0; i < fs.size(); i++) {
+        lbm_forest* f = fs[i];
+        std::copy(sn.cur[i].begin(), sn.cur[i].end(), f->cur);
+        for (int L = 0; L < f->plan.nlev; L++) {
+            const size_t bytes = size_t(f->dl[L].ncells) * Q * f->esize;
+            for (int g = 0; g < 2; g++, k++)
+                if (bytes) CU(cudaMemcpyAsync(f->dl[L].f[g], sn.bufs[k], bytes, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    CU(cudaStreamSynchronize(s));
+    return LBM_OK;
+}
+
+void free_snapshot(Snapshot& sn) {
+    for (void* p : sn.bufs) cudaFree(p);
+    sn.bufs.clear();
+}
+
+// Times n_steps of `step` for every (cells per thread, CTAs per SM) the kernels support and
+// keeps the fastest; `config` applies one.  Results do not depend on the configuration.
+template <typename Config, typename Step>
+lbm_status tune(const std::vector<lbm_forest*>& fs, cudaStream_t s, int LB, int n_steps, Config config, Step step,
+                int32_t* best_lzc, int32_t* best_minb, double* best_ms) {
+    Snapshot sn;
+    lbm_status st = take_snapshot(fs, s, sn);
+    if (st) {
+        free_snapshot(sn);
+        return st;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 1e300;
+    int bl = LB - 3 > 0 ? LB - 3 : 0, bm = 3;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(LBM_ECUDA, "cudaEventCreate failed");
+    for (int lzc = 0; lzc <= LB && !st; lzc++)
+        for (int minb = 2; minb <= 4 && !st; minb++) {
+            if ((st = config(lzc, minb)) || (st = step(1))) break;   // the first step captures the graphs
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(LBM_ECUDA, "cudaEventRecord failed");
+            if (!st) st = step(n_steps);
+            if (!st && cudaEventRecord(e1, s) != cudaSuccess) st = fail(LBM_ECUDA, "cudaEventRecord failed");
+            float ms = 0.f;
+            if (!st && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = fail(LBM_ECUDA, "timing a configuration failed");
+            if (!st && ms / n_steps < best) {
+                best = ms / n_steps;
+                bl = lzc;
+                bm = minb;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lbm_status rs = restore_snapshot(fs, s, sn);
+    free_snapshot(sn);
+    if (st) return st;
+    if (rs) return rs;
+    if ((st = config(bl, bm))) return st;
+    if (best_lzc) *best_lzc = bl;
+    if (best_minb) *best_minb = bm;
+    if (best_ms) *best_ms = best;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
+                                   double* ms_per_step) {
+    if (!f || n_steps < 1) return fail(LBM_EINVAL, "invalid argument");
+    if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
+        return fail(LBM_EINVAL, "set the level parameters and initialise every level before tuning");
+    if (f->timing) return fail(LBM_EINVAL, "timing is active");
+    return tune(
+        {f}, f->stream, f->plan.LB, n_steps, [&](int l, int m) { return lbm_set_kernel_config(f, l, m); },
+        [&](int n) { return lbm_step_coarse(f, n); }, cells_per_thread_log2, ctas_per_sm, ms_per_step);
+}
+
+// ------------------------------------------------------------------ batches of forests
+namespace {
+
+struct BatchPhase {
+    int level, substep, type;   // type 0: stream-collide F_L(substep), 1: explosion E_L
+    int n = 0, total = 0, grid = 0;
+    StepArgs* args[2] = {nullptr, nullptr};   // per level-0 parity
+    int* prefix = nullptr;
+};
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<lbm_forest*> fs;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    const Launchers* L = nullptr;
+    int nlev = 0, LB = 0, collision = 0, sms = 152;
+    int lzc = 2, minb = 3;
+    std::vector<BatchPhase> phases;
+    cudaGraphExec_t exec[2] = {};
+    int64_t updates = 0;
+};
+
+namespace {
+
+void free_phases(lbm_batch* b) {
+    for (int p = 0; p < 2; p++) {
+        if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+        b->exec[p] = nullptr;
+    }
+    for (BatchPhase& ph : b->phases) {
+        cudaFree(ph.args[0]);
+        cudaFree(ph.args[1]);
+        cudaFree(ph.prefix);
+    }
+    b->phases.clear();
+}
+
+// The phase list of one coarse step: Alg. 1 over the deepest member; a member without level L has
+// no work in the phases of level L.  Each phase holds, per member with work, the launch arguments
+// and grid of the member's own launch, for both level-0 parities.
+lbm_status build_phases(lbm_batch* b) {
+    free_phases(b);
+    const int B = 1 << b->LB;
+    // cells per thread per level: the largest up to the configured bound that gives about four
+    // waves of CTAs over the whole batch
+    std::vector<int> lzc(b->nlev);
+    for (int L = 0; L < b->nlev; L++) {
+        int64_t bricks = 0;
+        for (lbm_forest* f : b->fs)
+            if (L < f->plan.nlev) bricks += f->plan.lv[L].nown;
+        int z = b->lzc;
+        while (z > 0 && bricks * B * B * (B >> z) / 256 < int64_t(4) * b->sms * b->minb) z--;
+        lzc[L] = z;
+    }
+    std::vector<std::pair<int, int>> order;   // (level, substep), substep 0 = explosion
+    std::function<void(int)> rec = [&](int L) {
+        if (L == 0) {
+            if (b->nlev > 1) rec(1);
+            order.push_back({0, 1});
+            return;
+        }
+        order.push_back({L, 0});
+        if (L + 1 < b->nlev) rec(L + 1);
+        order.push_back({L, 1});
+        if (L + 1 < b->nlev) rec(L + 1);
+        order.push_back({L, 2});
+    };
+    rec(0);
+    std::vector<std::vector<StepArgs>> hargs[2];
+    std::vector<std::vector<int>> hprefix;
+    for (int p = 0; p < 2; p++) {
+        std::vector<std::vector<int>> cur(b->fs.size());
+        for (size_t i = 0; i < b->fs.size(); i++) {
+            cur[i].assign(b->fs[i]->cur, b->fs[i]->cur + LBM_MAX_LEVELS);
+            cur[i][0] = p;
+        }
+        for (const auto& o : order) {
+            const int L = o.first, s = o.second;
+            std::vector<StepArgs> args;
+            std::vector<int> prefix{0};
+            for (size_t i = 0; i < b->fs.size(); i++) {
+                lbm_forest* f = b->fs[i];
+                if (L >= f->plan.nlev) continue;
+                const HostLevel& V = f->plan.lv[L];
+                int grid;
+                if (s == 0) {
+                    grid = int((V.ework.size() / 4 + 255) / 256);
+                } else {
+                    const int64_t units = int64_t(V.nown) * B * B * (B >> lzc[L]);
+                    grid = int((units + 255) / 256) + int((V.gwork[s - 1].size() / 4 + 255) / 256);
+                }
+                if (grid > 0) {
+                    Launch l{L, s == 0 ? 0 : s, grid, s == 0 ? 1 : 0, lzc[L]};
+                    args.push_back(make_args(f, l, cur[i].data()));
+                    prefix.push_back(prefix.back() + grid);
+                }
+                if (s != 0) cur[i][L] ^= 1;
+            }
+            hargs[p].push_back(args);
+            if (p == 0) hprefix.push_back(prefix);
+        }
+    }
+    for (size_t k = 0; k < order.size(); k++) {
+        BatchPhase ph;
+        ph.level = order[k].first;
+        ph.substep = order[k].second;
+        ph.type = order[k].second == 0 ? 1 : 0;
+        ph.n = int(hargs[0][k].size());
+        ph.total = hprefix[k].back();
+        const int resident = b->sms * (ph.type == 1 ? 8 : b->minb);
+        ph.grid = std::min(ph.total, resident);
+        b->phases.push_back(ph);
+        BatchPhase& q = b->phases.back();
+        if (ph.n == 0) continue;
+        lbm_status st;
+        if ((st = upload(&q.args[0], hargs[0][k])) || (st = upload(&q.args[1], hargs[1][k])) ||
+            (st = upload(&q.prefix, hprefix[k])))
+            return st;
+    }
+    return LBM_OK;
+}
+
+lbm_status capture_batch(lbm_batch* b, int parity) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    for (const BatchPhase& ph : b->phases) {
+        if (ph.n == 0) continue;
+        if (ph.type == 1) b->L->explode_batch(ph.args[parity], ph.prefix, ph.n, ph.total, ph.grid, b->cap);
+        else b->L->step_batch(ph.args[parity], ph.prefix, ph.n, ph.total, ph.grid, b->collision, b->LB, b->minb, b->cap);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LBM_ECUDA, "batch capture failed: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&b->exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(LBM_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(ie));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
+    free_phases(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!forests || n < 1) return fail(LBM_EINVAL, "a batch needs at least one forest");
+    lbm_batch* b = new (std::nothrow) lbm_batch;
+    if (!b) return fail(LBM_ENOMEM, "host allocation failed");
+    const lbm_forest* f0 = forests[0];
+    for (int i = 0; i < n; i++) {
+        const lbm_forest* f = forests[i];
+        if (!f) {
+            delete b;
+            return fail(LBM_EINVAL, "forest %d is NULL", i);
+        }
+        if (f->plan.d.precision != f0->plan.d.precision || f->plan.d.collision != f0->plan.d.collision ||
+            f->plan.B != f0->plan.B || f->stream != f0->stream) {
+            delete b;
+            return fail(LBM_EINVAL, "forest %d differs from forest 0 in precision, collision, block size or stream", i);
+        }
+        for (int j = 0; j < i; j++)
+            if (forests[j] == f) {
+                delete b;
+                return fail(LBM_EINVAL, "forest %d appears twice", i);
+            }
+        b->fs.push_back(const_cast<lbm_forest*>(f));
+        b->nlev = std::max(b->nlev, f->plan.nlev);
+        b->updates += f->updates;
+    }
+    b->stream = f0->stream;
+    b->L = f0->L;
+    b->LB = f0->plan.LB;
+    b->collision = f0->plan.d.collision;
+    b->lzc = std::max(0, b->LB - 3);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return fail(LBM_ECUDA, "cannot create the capture stream");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_kernel_config(lbm_batch* b, int32_t cells_per_thread_log2, int32_t ctas_per_sm) {
+    if (!b) return fail(LBM_EINVAL, "batch is NULL");
+    if (cells_per_thread_log2 < 0 || cells_per_thread_log2 > b->LB)
+        return fail(LBM_EINVAL, "cells per thread must be 2^k with 2^k <= B");
+    if (ctas_per_sm < 2 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 2, 3 or 4");
+    CU(cudaStreamSynchronize(b->stream));
+    free_phases(b);
+    b->lzc = cells_per_thread_log2;
+    b->minb = ctas_per_sm;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n_steps) {
+    if (!b) return fail(LBM_EINVAL, "batch is NULL");
+    if (n_steps < 0) return fail(LBM_EINVAL, "negative step count");
+    const lbm_forest* f0 = b->fs[0];
+    for (size_t i = 0; i < b->fs.size(); i++) {
+        const lbm_forest* f = b->fs[i];
+        if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
+            return fail(LBM_EINVAL, "forest %d: set the level parameters and initialise every level", int(i));
+        if (f->timing) return fail(LBM_EINVAL, "forest %d: timing is active", int(i));
+        for (int L = 0; L < std::min(f->plan.nlev, f0->plan.nlev); L++)
+            if (f->cur[L] != f0->cur[L])
+                return fail(LBM_EINVAL, "forest %d is not at the two-grid parity of forest 0 (step members together)", int(i));
+        for (int L = f0->plan.nlev; L < f->plan.nlev; L++)
+            if (f->cur[L] != 0) return fail(LBM_EINVAL, "forest %d has an unexpected parity on level %d", int(i), L);
+    }
+    if (b->phases.empty()) {
+        lbm_status s = build_phases(b);
+        if (s) return s;
+    }
+    for (int k = 0; k < n_steps; k++) {
+        const int p = b->fs[0]->cur[0];
+        if (!b->exec[p]) {
+            lbm_status s = capture_batch(b, p);
+            if (s) return s;
+        }
+        CU(cudaGraphLaunch(b->exec[p], b->stream));
+        for (lbm_forest* f : b->fs) f->cur[0] ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_cell_updates_per_coarse_step(const lbm_batch* b, int64_t* n) {
+    if (!b || !n) return fail(LBM_EINVAL, "NULL argument");
+    *n = b->updates;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_launches_per_coarse_step(const lbm_batch* b, int32_t* n) {
+    if (!b || !n) return fail(LBM_EINVAL, "NULL argument");
+    if (b->phases.empty()) {
+        lbm_status s = build_phases(const_cast<lbm_batch*>(b));
+        if (s) return s;
+    }
+    int c = 0;
+    for (const BatchPhase& ph : b->phases) c += ph.n > 0;
+    *n = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
+                              double* ms_per_step) {
+    if (!b || n_steps < 1) return fail(LBM_EINVAL, "invalid argument");
+    return tune(
+        b->fs, b->stream, b->LB, n_steps, [&](int l, int m) { return lbm_batch_set_kernel_config(b, l, m); },
+        [&](int n) { return lbm_batch_step(b, n); }, cells_per_thread_log2, ctas_per_sm, ms_per_step);
+}
+
+}  // extern "C"

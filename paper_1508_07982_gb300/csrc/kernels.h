@@ -71,6 +71,11 @@ struct Launchers {
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
                    int grid, cudaStream_t s);
     void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s);
+    // One phase of a batch of forests: args[n] per forest, prefix[n+1] its first virtual CTA;
+    // `grid` persistent CTAs walk the `total` virtual CTAs.
+    void (*step_batch)(const StepArgs* args, const int* prefix, int n, int total, int grid, int collision, int LB,
+                       int minb, cudaStream_t s);
+    void (*explode_batch)(const StepArgs* args, const int* prefix, int n, int total, int grid, cudaStream_t s);
 };
 const Launchers& launchers_f64();
 const Launchers& launchers_f32();

@@ -56,8 +56,31 @@ struct LaunchImpl {
         if (lv.nework <= 0) return;
         explode_kernel<T><<<(lv.nework + 255) / 256, 256, 0, s>>>(lv, co, cur, cur_c);
     }
+    template <int COLL, int MINB>
+    static void step_batch_m(const StepArgs* args, const int* prefix, int n, int total, int grid, int LB, cudaStream_t s) {
+        if (LB == 3) step_batch_kernel<T, C, COLL, 3, MINB><<<grid, 256, 0, s>>>(args, prefix, n, total);
+        else if (LB == 4) step_batch_kernel<T, C, COLL, 4, MINB><<<grid, 256, 0, s>>>(args, prefix, n, total);
+        else step_batch_kernel<T, C, COLL, 5, MINB><<<grid, 256, 0, s>>>(args, prefix, n, total);
+    }
+    template <int COLL>
+    static void step_batch_b(const StepArgs* args, const int* prefix, int n, int total, int grid, int LB, int minb,
+                             cudaStream_t s) {
+        if (minb == 2) step_batch_m<COLL, 2>(args, prefix, n, total, grid, LB, s);
+        else if (minb == 4) step_batch_m<COLL, 4>(args, prefix, n, total, grid, LB, s);
+        else step_batch_m<COLL, 3>(args, prefix, n, total, grid, LB, s);
+    }
+    static void step_batch(const StepArgs* args, const int* prefix, int n, int total, int grid, int collision, int LB,
+                           int minb, cudaStream_t s) {
+        if (total <= 0 || grid <= 0) return;
+        if (collision == LBM_TRT) step_batch_b<LBM_TRT>(args, prefix, n, total, grid, LB, minb, s);
+        else step_batch_b<LBM_SRT>(args, prefix, n, total, grid, LB, minb, s);
+    }
+    static void explode_batch(const StepArgs* args, const int* prefix, int n, int total, int grid, cudaStream_t s) {
+        if (total <= 0 || grid <= 0) return;
+        explode_batch_kernel<T><<<grid, 256, 0, s>>>(args, prefix, n, total);
+    }
     static const Launchers& get() {
-        static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode};
+        static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode, &step_batch, &explode_batch};
         return L;
     }
 };

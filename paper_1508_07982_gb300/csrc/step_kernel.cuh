@@ -257,13 +257,20 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
 // per column, obstacle cells are skipped by a per-column bitmap, and a per-cell link mask (read
 // where the brick needs it) routes the few links that are not plain loads to pull_general.  CTAs
 // after the owned part cover the ghost work list of this sub-step.
-template <typename T, typename C, int COLL, int LB, int MINB>
-__global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
+// FP32 storage stages each cell's 19 pulls in shared memory with cp.async, two cells deep; the
+// other storage types load into registers.  The same array receives general-pull values.
+template <typename T, typename C>
+struct StepSmem {
+    static constexpr bool kAsync = sizeof(T) == 4;
+    C slow[kAsync ? 2 : 1][19][256];
+};
+
+// The work of CTA `bid` of one launch of F_L(s) (see step_kernel); every thread of the CTA calls it.
+template <typename T, typename C, int COLL, int LB>
+__device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepSmem<T, C>& smem) {
     constexpr int B = 1 << LB, M = B - 1, B2s = 2 * LB, B3s = 3 * LB;
-    // FP32 storage stages each cell's 19 pulls in shared memory with cp.async, two cells deep;
-    // the other storage types load into registers.  The same array receives general-pull values.
-    constexpr bool kAsync = sizeof(T) == 4;
-    __shared__ C slow[kAsync ? 2 : 1][19][256];
+    constexpr bool kAsync = StepSmem<T, C>::kAsync;
+    auto& slow = smem.slow;
     const int zc = 1 << a.lzc;
     const int upb = (1 << B2s) << (LB - a.lzc);            // units (column chunks) per brick
     const int64_t owned_units = int64_t(a.lv.nown) * upb;
@@ -274,8 +281,8 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     const Access<T, C> acc{a, LB, M};
     const int tid = threadIdx.x;
 
-    if (int64_t(blockIdx.x) < owned_ctas) {
-        const int64_t u = int64_t(blockIdx.x) * 256 + tid;
+    if (bid < owned_ctas) {
+        const int64_t u = bid * 256 + tid;
         if (u >= owned_units) return;
         const int brick = int(u / upb);
         const int r = int(u - int64_t(brick) * upb);
@@ -402,7 +409,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
     // ghost layers 1-2: stream only, the directions the work entry needs; a source holding an
     // exploded value is read from the coarse parent, and bounce-back/wall links take the general pull
     const int gs = a.substep - 1;
-    const int i = int(int64_t(blockIdx.x - owned_ctas) * 256 + tid);
+    const int i = int((bid - owned_ctas) * 256 + tid);
     if (i >= a.lv.ngwork[gs]) return;
     const uint4 e = __ldg(a.lv.gwork[gs] + i);
     const int c = int(e.x);
@@ -441,12 +448,48 @@ __global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
         if ((need >> q) & 1u) Store<T>::st(p + int64_t(q) * n, v[q]);
 }
 
+template <typename T, typename C, int COLL, int LB, int MINB>
+__global__ void __launch_bounds__(256, MINB) step_kernel(const StepArgs a) {
+    __shared__ StepSmem<T, C> sm;
+    step_block<T, C, COLL, LB>(a, blockIdx.x, sm);
+}
+
+// Copies the launch arguments of the forest that owns virtual CTA v of a batched phase into shared
+// memory; returns v's index within that forest's launch.  prefix[k] is the first virtual CTA of
+// forest k (prefix[0] = 0, prefix[n] = the phase's total).  Every thread of the CTA calls it.
+__device__ __forceinline__ int64_t batch_args(const StepArgs* args, const int* prefix, int n, int v, StepArgs& sa) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= v) lo = mid;
+        else hi = mid;
+    }
+    __syncthreads();   // the previous iteration's readers of sa are done
+    constexpr int words = int(sizeof(StepArgs) / 4);
+    const int* s = reinterpret_cast<const int*>(args + lo);
+    int* d = reinterpret_cast<int*>(&sa);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) d[w] = __ldg(s + w);
+    __syncthreads();
+    return int64_t(v - __ldg(prefix + lo));
+}
+
+// One phase F_L(s) of a batch of forests in one persistent launch: virtual CTA v of the phase
+// (v < total) is CTA v - prefix[k] of forest k's own launch, with forest k's arguments.
+template <typename T, typename C, int COLL, int LB, int MINB>
+__global__ void __launch_bounds__(256, MINB) step_batch_kernel(const StepArgs* args, const int* prefix, int n, int total) {
+    __shared__ StepSmem<T, C> sm;
+    __shared__ StepArgs sa;
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int64_t bid = batch_args(args, prefix, n, v, sa);
+        step_block<T, C, COLL, LB>(sa, bid, sm);
+    }
+}
+
 // Explosion (Eq. ctof) at the start of every visit of a finer level: the ghost-layer-1 values
 // that owned cells pull in sub-step 1 take their coarse parent's post-collision PDFs, in the finer
 // level's current grid.  One thread per work entry, one predicated copy per direction it lists.
 template <typename T>
-__global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void explode_entry(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, int i) {
     if (i >= lv.nework) return;
     const uint4 e = __ldg(lv.ework + i);
     const T* src = static_cast<const T*>(co.f[cur_c]) + e.z;
@@ -458,6 +501,21 @@ __global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const D
 #pragma unroll
     for (int q = 1; q < 19; q++)
         if ((e.y >> q) & 1u) dst[int64_t(q) * lv.ncells] = v[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) explode_kernel(const DevLevel lv, const DevLevel co, int cur, int cur_c) {
+    explode_entry<T>(lv, co, cur, cur_c, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// E_L of a batch of forests in one persistent launch (virtual CTAs as in step_batch_kernel).
+template <typename T>
+__global__ void __launch_bounds__(256) explode_batch_kernel(const StepArgs* args, const int* prefix, int n, int total) {
+    __shared__ StepArgs sa;
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int64_t bid = batch_args(args, prefix, n, v, sa);
+        explode_entry<T>(sa.lv, sa.co, sa.cur, sa.cur_c, int(bid) * 256 + threadIdx.x);
+    }
 }
 
 // Equilibrium start (Eq. fequ) followed by one collision, so the stored state is post-collision.

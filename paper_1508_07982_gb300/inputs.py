@@ -47,6 +47,49 @@ def cavity_case(lid=0.05, lambda_e0=1.6, B=8):
                 lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0))
 
 
+def batch_cases(n=256, seed=SEED, B=16):
+    """Small lid-driven cavities for stepping many forests together (the batched workload).
+
+    Per case, drawn in turn from one seeded stream and redrawn until the leaf count lies in
+    [8, 64]: root blocks per axis in {1..4}; 2 or 3 levels; lambda_e0 ~ U(1.5, 1.9); lid speed
+    ~ U(0.02, 0.08) along x on the z+ face, no-slip elsewhere; TRT with Lambda = 3/16.  Level 1
+    refines one random box of root blocks.  Level 2 refines one random box of level-1 blocks inside
+    it, one level-1 block away from the level-1 box's faces (except where it reaches a wall), so
+    that the forest is 2:1 balanced as drawn and its leaf count is known without building it:
+    roots + 7 |box 1| + 7 |box 2|.  Each case carries that count as "leaves".
+    """
+    rng = np.random.default_rng(seed)
+    cases = []
+    while len(cases) < n:
+        r = rng.integers(1, 5, size=3)
+        lmax = int(rng.integers(1, 3))
+        lo1 = np.array([rng.integers(0, r[a]) for a in range(3)])
+        hi1 = np.array([rng.integers(lo1[a] + 1, r[a] + 1) for a in range(3)])
+        n1 = int(np.prod(hi1 - lo1))
+        regions = [("box", 1, tuple(int(v) * B for v in lo1), tuple(int(v) * B for v in hi1))]
+        n2 = 0
+        if lmax == 2:
+            a_lo = 2 * lo1 + (lo1 > 0)
+            a_hi = 2 * hi1 - (hi1 < r)
+            if np.any(a_hi <= a_lo):
+                continue
+            lo2 = np.array([rng.integers(a_lo[a], a_hi[a]) for a in range(3)])
+            hi2 = np.array([rng.integers(lo2[a] + 1, a_hi[a] + 1) for a in range(3)])
+            n2 = int(np.prod(hi2 - lo2))
+            regions.append(("box", 2, tuple(int(v) * B // 2 for v in lo2), tuple(int(v) * B // 2 for v in hi2)))
+        leaves = int(np.prod(r)) + 7 * n1 + 7 * n2
+        if not 8 <= leaves <= 64:
+            continue
+        lambda_e0 = float(rng.uniform(1.5, 1.9))
+        lid = float(rng.uniform(0.02, 0.08))
+        cases.append(dict(root=tuple(int(v) for v in r), B=B, lmax=lmax, collision="trt", rho0=1.0,
+                          bc=["noslip"] * 5 + ["velocity"],
+                          bc_u=[(0.0, 0.0, 0.0)] * 5 + [(lid, 0.0, 0.0)],
+                          spheres=[], regions=regions, lambda_e0=lambda_e0, magic=3.0 / 16.0,
+                          accel=(0.0, 0.0, 0.0), leaves=leaves))
+    return cases
+
+
 def periodic_case(n=64, B=16, collision="srt", omega=1.9, regions=(), lmax=0):
     """Fully periodic cube of n^3 level-0 cells (uniform unless regions refine it)."""
     r = n // B

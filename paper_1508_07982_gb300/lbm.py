@@ -28,7 +28,9 @@ EXPORTS = [
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
     "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
-    "lbm_mass_momentum_noalloc",
+    "lbm_mass_momentum_noalloc", "lbm_autotune", "lbm_batch_create", "lbm_batch_step",
+    "lbm_batch_set_kernel_config", "lbm_batch_autotune", "lbm_batch_cell_updates_per_coarse_step",
+    "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy",
 ]
 NOALLOC_MAX_CELLS = 16384 * 4096
 
@@ -102,6 +104,14 @@ def library():
             "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_get_kernel_config": [P, i32p, i32p],
             "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, P, P],
+            "lbm_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
+            "lbm_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P)],
+            "lbm_batch_step": [P, ctypes.c_int32],
+            "lbm_batch_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
+            "lbm_batch_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
+            "lbm_batch_cell_updates_per_coarse_step": [P, i64p],
+            "lbm_batch_launches_per_coarse_step": [P, i32p],
+            "lbm_batch_destroy": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -369,6 +379,13 @@ class Forest:
         _check(library().lbm_get_kernel_config(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    def autotune(self, n_steps=10):
+        """lbm_autotune: applies the fastest thread mapping; returns (cells_per_thread_log2,
+        ctas_per_sm, ms per coarse step).  The state is left as it was."""
+        a, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(library().lbm_autotune(self.h, n_steps, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)))
+        return a.value, b.value, ms.value
+
     def timing_begin(self, max_steps):
         _check(library().lbm_timing_begin(self.h, max_steps))
 
@@ -382,3 +399,47 @@ class Forest:
         i64 = ctypes.POINTER(ctypes.c_int64)
         _check(library().lbm_timing_end(self.h, _dp(ms), cnt.ctypes.data_as(i64), _dp(ems), ecnt.ctypes.data_as(i64)))
         return (ms, cnt, ems, ecnt) if explode else (ms, cnt)
+
+
+class Batch:
+    """Independent forests stepped together, one launch per phase (lbm_batch_create ...
+    lbm_batch_destroy).  The forests stay usable one by one and must outlive the batch."""
+
+    def __init__(self, forests):
+        self.forests = list(forests)
+        arr = (ctypes.c_void_p * len(self.forests))(*[f.h.value for f in self.forests])
+        h = ctypes.c_void_p()
+        _check(library().lbm_batch_create(arr, len(self.forests), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(library().lbm_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_steps=1):
+        _check(library().lbm_batch_step(self.h, n_steps))
+
+    def set_kernel_config(self, cells_per_thread_log2, ctas_per_sm):
+        _check(library().lbm_batch_set_kernel_config(self.h, cells_per_thread_log2, ctas_per_sm))
+
+    def autotune(self, n_steps=10):
+        a, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(library().lbm_batch_autotune(self.h, n_steps, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)))
+        return a.value, b.value, ms.value
+
+    def cell_updates_per_coarse_step(self):
+        n = ctypes.c_int64()
+        _check(library().lbm_batch_cell_updates_per_coarse_step(self.h, ctypes.byref(n)))
+        return n.value
+
+    def launches_per_coarse_step(self):
+        n = ctypes.c_int32()
+        _check(library().lbm_batch_launches_per_coarse_step(self.h, ctypes.byref(n)))
+        return n.value
