@@ -243,6 +243,44 @@ lbm_status lbm_batch_cell_updates_per_coarse_step(const lbm_batch* b, int64_t* n
 lbm_status lbm_batch_launches_per_coarse_step(const lbm_batch* b, int32_t* n);
 lbm_status lbm_batch_destroy(lbm_batch* b);
 
+/* ---- learned warm start: a 3-D convolutional net -------------------------------------------
+ * The paper has no learned component; this net serves the warm start of the refined levels.  It
+ * maps the coarse-only solution, upsampled onto a refined block plus a halo, to the refined
+ * solution there; lbm_init_equilibrium then starts the refined levels from f^eq of its output
+ * (Eq. fequ), and the LBM itself runs unmodified.
+ *
+ * Net: `layers` 3x3x3 convolutions, zero padding, width 16, ReLU between layers and none after
+ * the last.  Layer 0 reads the first `in_channels` channels, the last layer writes the first
+ * `out_channels`.  Activations are device tensors of `nvol` volumes of D x H x W voxels, x fastest,
+ * channels last with 16 BF16 channels per voxel (unused channels zero): [nvol][D][H][W][16].  The
+ * products run on the tensor cores with BF16 operands and FP32 accumulation; each layer's output
+ * is rounded to BF16.  Parameters are FP32, per layer W[27][16 out][16 in] (tap o = (dz+1)*9 +
+ * (dy+1)*3 + (dx+1)) then b[16]; lbm_net_num_params counts them, get/set copy them to/from host
+ * memory.  Weights start He-uniform from a SplitMix64 stream seeded by `seed`.
+ *
+ * lbm_net_forward writes the last layer's BF16 output z.  lbm_net_predict writes the FP32
+ * prediction pred[N][out_channels] = skip + z (skip FP32 [N][out_channels], may be NULL).
+ * lbm_net_gradient (after a forward or predict call on the same input) computes the mean squared
+ * error of that prediction against target[N][out_channels] over the voxels weight[N] marks (NULL:
+ * all; the mean divides by sum(weight) x out_channels) and the gradients of every parameter
+ * (lbm_net_get_grads); lbm_net_train_step does forward, gradient and one Adam step (beta 0.9 /
+ * 0.999, eps 1e-8) with learning rate lr.  All pointers except the host parameter buffers are
+ * device pointers; calls run on `stream` and synchronise it where they return a loss. */
+typedef struct lbm_net lbm_net;
+lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_channels, uint64_t seed, void* stream,
+                          lbm_net** out);
+lbm_status lbm_net_destroy(lbm_net* n);
+lbm_status lbm_net_num_params(const lbm_net* n, int64_t* count);
+lbm_status lbm_net_get_params(const lbm_net* n, float* host);
+lbm_status lbm_net_set_params(lbm_net* n, const float* host);
+lbm_status lbm_net_forward(lbm_net* n, const void* x, int32_t D, int32_t H, int32_t W, int32_t nvol, void* z);
+lbm_status lbm_net_predict(lbm_net* n, const void* x, const float* skip, int32_t D, int32_t H, int32_t W, int32_t nvol,
+                           float* pred);
+lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, const float* weight, double* loss);
+lbm_status lbm_net_get_grads(const lbm_net* n, float* host);
+lbm_status lbm_net_train_step(lbm_net* n, const void* x, const float* skip, const float* target, const float* weight,
+                              int32_t D, int32_t H, int32_t W, int32_t nvol, float lr, double* loss);
+
 /* ---- totals without allocation ------------------------------------------------------------
  * The paper has no counterpart: this entry point serves callers that cannot allocate device
  * memory when they need mass and momentum totals (code running during CUDA stream capture,

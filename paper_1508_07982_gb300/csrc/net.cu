@@ -1,0 +1,514 @@
+// Learned warm start: a 3-D convolutional net that maps the coarse-only solution, upsampled onto a
+// refined block (plus a halo), to the refined solution there.  The net's output initialises the
+// refined levels with f = f^eq(rho, u) (Eq. fequ); the LBM then runs unmodified.
+//
+// Net: L layers of 3x3x3 convolutions (zero padding, stride 1), width 16, ReLU between layers,
+// none after the last.  Tensors are channels-last volumes of 16 BF16 channels (32 bytes per
+// voxel), `nvol` volumes of D x H x W voxels stored one after another, x fastest.  Products
+// run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulate).  Weights are kept
+// in FP32 (master copy, Adam moments) and rounded to BF16 for the products.
+//
+//   forward   Z_l = b_l + sum_o W_l[o] X_l[v + o]          X_{l+1} = relu(Z_l)
+//   backward  dW_l[o] += sum_v dZ_l[v] (x) X_l[v + o]      db_l = sum_v dZ_l[v]
+//             dX_l[v] = sum_o W_l[o]^T dZ_l[v - o]         dZ_{l-1} = dX_l * [X_l > 0]
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr int CH = 16;       // channels of every tensor (unused channels are zero)
+constexpr int TAPS = 27;     // 3x3x3 offsets, o = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+
+struct Dims {
+    int D, H, W;   // voxels per volume along z, y, x
+    int nvol;      // volumes
+    long long V;   // voxels per volume
+    long long N;   // all voxels
+};
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Linear index of voxel v shifted by tap o, or -1 outside its volume (zero padding).
+__device__ __forceinline__ long long shifted(const Dims& d, long long v, int o) {
+    if (v >= d.N) return -1;
+    const long long vol = v / d.V;
+    long long r = v - vol * d.V;
+    const int x = int(r % d.W);
+    r /= d.W;
+    const int y = int(r % d.H), z = int(r / d.H);
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int sx = x + dx, sy = y + dy, sz = z + dz;
+    if (sx < 0 || sx >= d.W || sy < 0 || sy >= d.H || sz < 0 || sz >= d.D) return -1;
+    return vol * d.V + ((long long)(sz) * d.H + sy) * d.W + sx;
+}
+
+// Z[v][n] = bias[n] + sum_o sum_k Wt[o][n][k] X[v + o][k] over 16 voxels per warp; then
+// optionally relu (act = 1) or multiplication by [mask > 0] (act = 2, the ReLU derivative of the
+// layer whose output `mask` is).  Wt is BF16 [27][16 out][16 in].
+__global__ void __launch_bounds__(256) conv_kernel(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
+                                                   const float* __restrict__ bias, __nv_bfloat16* __restrict__ Z, Dims d,
+                                                   int act, const __nv_bfloat16* __restrict__ mask) {
+    __shared__ uint32_t sw[TAPS * CH * CH / 2];
+    for (int i = threadIdx.x; i < TAPS * CH * CH / 2; i += blockDim.x) sw[i] = reinterpret_cast<const uint32_t*>(Wt)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long v0 = ((long long)(blockIdx.x) * 8 + (threadIdx.x >> 5)) * 16;
+    if (v0 >= d.N) return;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const uint32_t* X32 = reinterpret_cast<const uint32_t*>(X);
+    for (int o = 0; o < TAPS; o++) {
+        const long long r0 = shifted(d, v0 + g, o), r1 = shifted(d, v0 + g + 8, o);
+        uint32_t a[4];
+        a[0] = r0 >= 0 ? __ldg(X32 + r0 * (CH / 2) + t) : 0u;
+        a[1] = r1 >= 0 ? __ldg(X32 + r1 * (CH / 2) + t) : 0u;
+        a[2] = r0 >= 0 ? __ldg(X32 + r0 * (CH / 2) + t + 4) : 0u;
+        a[3] = r1 >= 0 ? __ldg(X32 + r1 * (CH / 2) + t + 4) : 0u;
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            const int n = nt * 8 + g;
+            const uint32_t b0 = sw[(o * CH + n) * (CH / 2) + t], b1 = sw[(o * CH + n) * (CH / 2) + t + 4];
+            mma16816(acc[nt], a, b0, b1);
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const long long v = v0 + g + 8 * h;
+            if (v >= d.N) continue;
+            const int n = nt * 8 + 2 * t;
+            float z0 = acc[nt][2 * h] + (bias ? bias[n] : 0.f), z1 = acc[nt][2 * h + 1] + (bias ? bias[n + 1] : 0.f);
+            if (act == 1) {
+                z0 = fmaxf(z0, 0.f);
+                z1 = fmaxf(z1, 0.f);
+            } else if (act == 2) {
+                const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mask)[v * (CH / 2) + n / 2];
+                if (!(__bfloat162float(m.x) > 0.f)) z0 = 0.f;
+                if (!(__bfloat162float(m.y) > 0.f)) z1 = 0.f;
+            }
+            reinterpret_cast<__nv_bfloat162*>(Z)[v * (CH / 2) + n / 2] = __floats2bfloat162_rn(z0, z1);
+        }
+}
+
+// dW[o][m][n] += sum_v dZ[v][m] X[v + o][n] and db[m] += sum_v dZ[v][m].  Block (chunk, o): 8 warps,
+// each over its share of the chunk's voxels in steps of 16; partial sums are added with atomics.
+__global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dZ,
+                                                    float* __restrict__ dW, float* __restrict__ db, Dims d, long long chunk) {
+    const int o = blockIdx.y;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
+    const long long begin = (long long)(blockIdx.x) * chunk, end = begin + chunk < d.N ? begin + chunk : d.N;
+    const unsigned short* Xs = reinterpret_cast<const unsigned short*>(X);
+    const unsigned short* Ds = reinterpret_cast<const unsigned short*>(dZ);
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float bsum = 0.f;
+    for (long long v0 = begin + warp * 16; v0 < end; v0 += 8 * 16) {
+        // A[m][k] = dZ[v0 + k][m]; B[k][n] = X[v0 + k + o][n]
+        auto dz = [&](int k, int m) -> uint32_t {
+            const long long v = v0 + k;
+            return v < end ? uint32_t(__ldg(Ds + v * CH + m)) : 0u;
+        };
+        auto xs = [&](int k, int n) -> uint32_t {
+            const long long v = v0 + k;
+            if (v >= end) return 0u;
+            const long long r = shifted(d, v, o);
+            return r >= 0 ? uint32_t(__ldg(Xs + r * CH + n)) : 0u;
+        };
+        uint32_t a[4];
+        a[0] = dz(2 * t, g) | (dz(2 * t + 1, g) << 16);
+        a[1] = dz(2 * t, g + 8) | (dz(2 * t + 1, g + 8) << 16);
+        a[2] = dz(2 * t + 8, g) | (dz(2 * t + 9, g) << 16);
+        a[3] = dz(2 * t + 8, g + 8) | (dz(2 * t + 9, g + 8) << 16);
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+            const int n = nt * 8 + g;
+            const uint32_t b0 = xs(2 * t, n) | (xs(2 * t + 1, n) << 16);
+            const uint32_t b1 = xs(2 * t + 8, n) | (xs(2 * t + 9, n) << 16);
+            mma16816(acc[nt], a, b0, b1);
+        }
+        if (o == 13 && lane < 16)
+            for (int k = 0; k < 16; k++) {
+                const long long v = v0 + k;
+                if (v < end) bsum += __bfloat162float(__ushort_as_bfloat16(__ldg(Ds + v * CH + lane)));
+            }
+    }
+    __shared__ float red[8][CH * CH];
+    __shared__ float bred[8][CH];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int m = g + 8 * h, n = nt * 8 + 2 * t;
+            red[warp][m * CH + n] = acc[nt][2 * h];
+            red[warp][m * CH + n + 1] = acc[nt][2 * h + 1];
+        }
+    if (lane < 16) bred[warp][lane] = bsum;
+    __syncthreads();
+    for (int i = threadIdx.x; i < CH * CH; i += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < 8; w++) s += red[w][i];
+        atomicAdd(dW + o * CH * CH + i, s);
+    }
+    if (o == 13 && threadIdx.x < CH) {
+        float s = 0.f;
+        for (int w = 0; w < 8; w++) s += bred[w][threadIdx.x];
+        atomicAdd(db + threadIdx.x, s);
+    }
+}
+
+// Master FP32 weights [27][16 out][16 in] -> BF16 copies for the forward product and, flipped and
+// transposed, for the backward data product: Wb[o'][k][m] = W[26 - o'][m][k].
+__global__ void weights_kernel(const float* __restrict__ W, __nv_bfloat16* __restrict__ Wf, __nv_bfloat16* __restrict__ Wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TAPS * CH * CH) return;
+    const int o = i / (CH * CH), m = (i / CH) % CH, k = i % CH;
+    const __nv_bfloat16 w = __float2bfloat16_rn(W[i]);
+    Wf[i] = w;
+    Wb[((TAPS - 1 - o) * CH + k) * CH + m] = w;
+}
+
+// Adam (Kingma & Ba 2015) with bias correction, on n parameters.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m, float* __restrict__ v,
+                            int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gr = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gr, vi = b2 * v[i] + (1.f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Prediction = skip + Z (first `nout` channels) over the voxels `weight` marks; squared error
+// against the target, summed in FP64; dZ = 2 weight (pred - target) / count as BF16 (other
+// channels 0).  pred (FP32 [N][nout]) may be NULL.
+__global__ void __launch_bounds__(256) loss_kernel(const __nv_bfloat16* __restrict__ Z, const float* __restrict__ skip,
+                                                   const float* __restrict__ target, const float* __restrict__ weight,
+                                                   long long N, int nout, float inv_count, __nv_bfloat16* __restrict__ dZ,
+                                                   float* __restrict__ pred, double* __restrict__ loss) {
+    const long long v = (long long)(blockIdx.x) * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (v < N) {
+        const float w = weight ? weight[v] : 1.f;
+        for (int c = 0; c < CH; c++) {
+            float g = 0.f;
+            if (c < nout) {
+                const float p = __bfloat162float(Z[v * CH + c]) + (skip ? skip[v * nout + c] : 0.f);
+                if (pred) pred[v * nout + c] = p;
+                if (target) {
+                    const float e = p - target[v * nout + c];
+                    s += double(w) * double(e) * double(e);
+                    g = 2.f * w * e * inv_count;
+                }
+            }
+            if (dZ) dZ[v * CH + c] = __float2bfloat16_rn(g);
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (int(threadIdx.x) < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0]);
+}
+
+// ---------------------------------------------------------------- host side
+
+lbm_status nfail(lbm_status s, const char* msg) {
+    lbm::set_last_error(msg);
+    return s;
+}
+
+#define NCU(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            char b_[256];                                                              \
+            snprintf(b_, sizeof b_, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+            return nfail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, b_); \
+        }                                                                              \
+    } while (0)
+
+// SplitMix64 (Steele, Lea & Flood 2014), for the weight initialisation.
+uint64_t splitmix(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct lbm_net {
+    int layers = 0, cin = 0, cout = 0;
+    cudaStream_t stream = nullptr;
+    float* params = nullptr;   // per layer: W [27][16][16], b [16]
+    float* grads = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    __nv_bfloat16* wf = nullptr;   // per layer: forward BF16 weights
+    __nv_bfloat16* wb = nullptr;   // per layer: backward-data BF16 weights
+    int64_t step = 0;
+    // activations of the last forward pass: X_0 .. X_{L-1}, Z_{L-1}; and two gradient buffers
+    std::vector<__nv_bfloat16*> act;
+    __nv_bfloat16* g0 = nullptr;
+    __nv_bfloat16* g1 = nullptr;
+    long long cap = 0;       // voxels the activation buffers hold
+    double* d_loss = nullptr;
+    double* h_loss = nullptr;
+    Dims d{};
+};
+
+namespace {
+
+constexpr int PER_LAYER = TAPS * CH * CH + CH;
+
+void free_acts(lbm_net* n) {
+    for (auto* p : n->act) cudaFree(p);
+    n->act.clear();
+    cudaFree(n->g0);
+    cudaFree(n->g1);
+    n->g0 = n->g1 = nullptr;
+    n->cap = 0;
+}
+
+lbm_status ensure_acts(lbm_net* n, long long N) {
+    if (n->cap >= N) return LBM_OK;
+    free_acts(n);
+    const size_t bytes = size_t(N) * CH * sizeof(__nv_bfloat16);
+    for (int l = 0; l <= n->layers; l++) {
+        __nv_bfloat16* p = nullptr;
+        NCU(cudaMalloc(&p, bytes));
+        n->act.push_back(p);
+    }
+    NCU(cudaMalloc(&n->g0, bytes));
+    NCU(cudaMalloc(&n->g1, bytes));
+    n->cap = N;
+    return LBM_OK;
+}
+
+lbm_status refresh_weights(lbm_net* n) {
+    for (int l = 0; l < n->layers; l++)
+        weights_kernel<<<(TAPS * CH * CH + 255) / 256, 256, 0, n->stream>>>(
+            n->params + size_t(l) * PER_LAYER, n->wf + size_t(l) * TAPS * CH * CH, n->wb + size_t(l) * TAPS * CH * CH);
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status check_dims(int D, int H, int W, int nvol, Dims& d) {
+    if (D < 1 || H < 1 || W < 1 || nvol < 1) return nfail(LBM_EINVAL, "volume dimensions must be positive");
+    d.D = D;
+    d.H = H;
+    d.W = W;
+    d.nvol = nvol;
+    d.V = (long long)D * H * W;
+    d.N = d.V * nvol;
+    if (d.N > (1LL << 40)) return nfail(LBM_EINVAL, "too many voxels");
+    return LBM_OK;
+}
+
+// Forward pass over x (BF16 [N][16]); keeps every layer's input for the backward pass.
+lbm_status forward(lbm_net* n, const __nv_bfloat16* x, const Dims& d) {
+    lbm_status s = ensure_acts(n, d.N);
+    if (s) return s;
+    NCU(cudaMemcpyAsync(n->act[0], x, size_t(d.N) * CH * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice, n->stream));
+    const int grid = int((d.N + 127) / 128);
+    for (int l = 0; l < n->layers; l++) {
+        const float* b = n->params + size_t(l) * PER_LAYER + TAPS * CH * CH;
+        conv_kernel<<<grid, 256, 0, n->stream>>>(n->act[l], n->wf + size_t(l) * TAPS * CH * CH, b, n->act[l + 1], d,
+                                                 l + 1 < n->layers ? 1 : 0, nullptr);
+    }
+    NCU(cudaGetLastError());
+    n->d = d;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_channels, uint64_t seed, void* stream,
+                          lbm_net** out) {
+    if (!out) return nfail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (layers < 1 || layers > 16 || in_channels < 1 || in_channels > CH || out_channels < 1 || out_channels > CH)
+        return nfail(LBM_EINVAL, "layers must be 1..16 and channel counts 1..16");
+    lbm_net* n = new (std::nothrow) lbm_net;
+    if (!n) return nfail(LBM_ENOMEM, "host allocation failed");
+    n->layers = layers;
+    n->cin = in_channels;
+    n->cout = out_channels;
+    n->stream = static_cast<cudaStream_t>(stream);
+    const size_t np = size_t(layers) * PER_LAYER;
+    // He-uniform initialisation over the fan-in of each layer (27 taps x its input channels);
+    // channels beyond a layer's inputs or outputs keep zero weights
+    std::vector<float> h(np, 0.f);
+    uint64_t st = seed;
+    for (int l = 0; l < layers; l++) {
+        const int ci = l == 0 ? in_channels : CH, co = l + 1 == layers ? out_channels : CH;
+        const float bound = std::sqrt(6.f / float(TAPS * ci));
+        for (int o = 0; o < TAPS; o++)
+            for (int m = 0; m < co; m++)
+                for (int k = 0; k < ci; k++) {
+                    const double u = double(splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+                    h[size_t(l) * PER_LAYER + (o * CH + m) * CH + k] = float((2.0 * u - 1.0) * bound);
+                }
+    }
+    auto bail = [&](lbm_status s) {
+        std::string keep = lbm_last_error();
+        lbm_net_destroy(n);
+        lbm::set_last_error(keep.c_str());
+        return s;
+    };
+    if (cudaMalloc(&n->params, np * 4) != cudaSuccess || cudaMalloc(&n->grads, np * 4) != cudaSuccess ||
+        cudaMalloc(&n->m, np * 4) != cudaSuccess || cudaMalloc(&n->v, np * 4) != cudaSuccess ||
+        cudaMalloc(&n->wf, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
+        cudaMalloc(&n->wb, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
+        cudaMalloc(&n->d_loss, sizeof(double)) != cudaSuccess || cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess)
+        return bail(nfail(LBM_ENOMEM, "cannot allocate the net"));
+    if (cudaMemcpy(n->params, h.data(), np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(n->m, 0, np * 4) != cudaSuccess || cudaMemset(n->v, 0, np * 4) != cudaSuccess)
+        return bail(nfail(LBM_ECUDA, "cannot initialise the net"));
+    lbm_status s = refresh_weights(n);
+    if (s) return bail(s);
+    *out = n;
+    return LBM_OK;
+}
+
+lbm_status lbm_net_destroy(lbm_net* n) {
+    if (!n) return LBM_OK;
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    free_acts(n);
+    cudaFree(n->params);
+    cudaFree(n->grads);
+    cudaFree(n->m);
+    cudaFree(n->v);
+    cudaFree(n->wf);
+    cudaFree(n->wb);
+    cudaFree(n->d_loss);
+    if (n->h_loss) cudaFreeHost(n->h_loss);
+    delete n;
+    return LBM_OK;
+}
+
+lbm_status lbm_net_num_params(const lbm_net* n, int64_t* count) {
+    if (!n || !count) return nfail(LBM_EINVAL, "NULL argument");
+    *count = int64_t(n->layers) * PER_LAYER;
+    return LBM_OK;
+}
+
+lbm_status lbm_net_get_params(const lbm_net* n, float* host) {
+    if (!n || !host) return nfail(LBM_EINVAL, "NULL argument");
+    NCU(cudaStreamSynchronize(n->stream));
+    NCU(cudaMemcpy(host, n->params, size_t(n->layers) * PER_LAYER * 4, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_net_set_params(lbm_net* n, const float* host) {
+    if (!n || !host) return nfail(LBM_EINVAL, "NULL argument");
+    NCU(cudaStreamSynchronize(n->stream));
+    NCU(cudaMemcpy(n->params, host, size_t(n->layers) * PER_LAYER * 4, cudaMemcpyHostToDevice));
+    return refresh_weights(n);
+}
+
+lbm_status lbm_net_forward(lbm_net* n, const void* x, int32_t D, int32_t H, int32_t W, int32_t nvol, void* z) {
+    if (!n || !x || !z) return nfail(LBM_EINVAL, "NULL argument");
+    Dims d;
+    lbm_status s = check_dims(D, H, W, nvol, d);
+    if (s || (s = forward(n, static_cast<const __nv_bfloat16*>(x), d))) return s;
+    NCU(cudaMemcpyAsync(z, n->act[n->layers], size_t(d.N) * CH * 2, cudaMemcpyDeviceToDevice, n->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_net_predict(lbm_net* n, const void* x, const float* skip, int32_t D, int32_t H, int32_t W, int32_t nvol,
+                           float* pred) {
+    if (!n || !x || !pred) return nfail(LBM_EINVAL, "NULL argument");
+    Dims d;
+    lbm_status s = check_dims(D, H, W, nvol, d);
+    if (s || (s = forward(n, static_cast<const __nv_bfloat16*>(x), d))) return s;
+    loss_kernel<<<int((d.N + 255) / 256), 256, 0, n->stream>>>(n->act[n->layers], skip, nullptr, nullptr, d.N, n->cout,
+                                                               0.f, nullptr, pred, nullptr);
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_net_train_step(lbm_net* n, const void* x, const float* skip, const float* target, const float* weight,
+                              int32_t D, int32_t H, int32_t W, int32_t nvol, float lr, double* loss) {
+    if (!n || !x || !target) return nfail(LBM_EINVAL, "NULL argument");
+    Dims d;
+    lbm_status s = check_dims(D, H, W, nvol, d);
+    if (s || (s = forward(n, static_cast<const __nv_bfloat16*>(x), d))) return s;
+    lbm_status r = lbm_net_gradient(n, skip, target, weight, loss);
+    if (r) return r;
+    n->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = float(1.0 - std::pow(double(b1), double(n->step))), c2 = float(1.0 - std::pow(double(b2), double(n->step)));
+    const int np = n->layers * PER_LAYER;
+    adam_kernel<<<(np + 255) / 256, 256, 0, n->stream>>>(n->params, n->grads, n->m, n->v, np, lr, b1, b2, 1e-8f, c1, c2);
+    NCU(cudaGetLastError());
+    return refresh_weights(n);
+}
+
+lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, const float* weight, double* loss) {
+    if (!n || !target) return nfail(LBM_EINVAL, "NULL argument");
+    if (n->act.empty() || n->d.N == 0) return nfail(LBM_EINVAL, "run a forward pass first");
+    const Dims& d = n->d;
+    // count of weighted target values (the MSE denominator)
+    double count = 0.0;
+    if (weight) {
+        std::vector<float> hw(size_t(d.N));
+        NCU(cudaMemcpyAsync(hw.data(), weight, size_t(d.N) * 4, cudaMemcpyDeviceToHost, n->stream));
+        NCU(cudaStreamSynchronize(n->stream));
+        for (float w : hw) count += w;
+    } else {
+        count = double(d.N);
+    }
+    count *= n->cout;
+    if (!(count > 0.0)) return nfail(LBM_EINVAL, "the loss weights are all zero");
+    NCU(cudaMemsetAsync(n->d_loss, 0, sizeof(double), n->stream));
+    NCU(cudaMemsetAsync(n->grads, 0, size_t(n->layers) * PER_LAYER * 4, n->stream));
+    loss_kernel<<<int((d.N + 255) / 256), 256, 0, n->stream>>>(n->act[n->layers], skip, target, weight, d.N, n->cout,
+                                                               float(1.0 / count), n->g0, nullptr, n->d_loss);
+    const int grid = int((d.N + 127) / 128);
+    const long long chunk = 4096;
+    const dim3 wg(unsigned((d.N + chunk - 1) / chunk), TAPS);
+    __nv_bfloat16* dz = n->g0;
+    __nv_bfloat16* dx = n->g1;
+    for (int l = n->layers - 1; l >= 0; l--) {
+        float* gw = n->grads + size_t(l) * PER_LAYER;
+        wgrad_kernel<<<wg, 256, 0, n->stream>>>(n->act[l], dz, gw, gw + TAPS * CH * CH, d, chunk);
+        if (l > 0) {
+            conv_kernel<<<grid, 256, 0, n->stream>>>(dz, n->wb + size_t(l) * TAPS * CH * CH, nullptr, dx, d, 2, n->act[l]);
+            std::swap(dz, dx);
+        }
+    }
+    NCU(cudaGetLastError());
+    NCU(cudaMemcpyAsync(n->h_loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    NCU(cudaStreamSynchronize(n->stream));
+    if (loss) *loss = *n->h_loss / count;
+    return LBM_OK;
+}
+
+lbm_status lbm_net_get_grads(const lbm_net* n, float* host) {
+    if (!n || !host) return nfail(LBM_EINVAL, "NULL argument");
+    NCU(cudaStreamSynchronize(n->stream));
+    NCU(cudaMemcpy(host, n->grads, size_t(n->layers) * PER_LAYER * 4, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,9 @@ EXPORTS = [
     "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
     "lbm_mass_momentum_noalloc", "lbm_autotune", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_set_kernel_config", "lbm_batch_autotune", "lbm_batch_cell_updates_per_coarse_step",
-    "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy",
+    "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy", "lbm_net_create", "lbm_net_destroy",
+    "lbm_net_num_params", "lbm_net_get_params", "lbm_net_set_params", "lbm_net_forward", "lbm_net_predict",
+    "lbm_net_gradient", "lbm_net_get_grads", "lbm_net_train_step",
 ]
 NOALLOC_MAX_CELLS = 16384 * 4096
 
@@ -112,6 +114,17 @@ def library():
             "lbm_batch_cell_updates_per_coarse_step": [P, i64p],
             "lbm_batch_launches_per_coarse_step": [P, i32p],
             "lbm_batch_destroy": [P],
+            "lbm_net_create": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, ctypes.POINTER(P)],
+            "lbm_net_destroy": [P],
+            "lbm_net_num_params": [P, i64p],
+            "lbm_net_get_params": [P, P],
+            "lbm_net_set_params": [P, P],
+            "lbm_net_forward": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P],
+            "lbm_net_predict": [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P],
+            "lbm_net_gradient": [P, P, P, P, dp],
+            "lbm_net_get_grads": [P, P],
+            "lbm_net_train_step": [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_float, dp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -443,3 +456,77 @@ class Batch:
         n = ctypes.c_int32()
         _check(library().lbm_batch_launches_per_coarse_step(self.h, ctypes.byref(n)))
         return n.value
+
+
+class Net:
+    """The warm-start convolutional net (lbm_net_create ... lbm_net_destroy).  Volumes are torch
+    tensors on the device: inputs BF16 [nvol, D, H, W, 16]; skip, target FP32 [nvol, D, H, W, out];
+    weight FP32 [nvol, D, H, W]."""
+
+    def __init__(self, layers=5, in_channels=6, out_channels=4, seed=20150827, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        _check(library().lbm_net_create(layers, in_channels, out_channels, seed, ctypes.c_void_p(stream),
+                                        ctypes.byref(h)))
+        self.h = h
+        self.layers, self.in_channels, self.out_channels = layers, in_channels, out_channels
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(library().lbm_net_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        n = ctypes.c_int64()
+        _check(library().lbm_net_num_params(self.h, ctypes.byref(n)))
+        return n.value
+
+    def params(self):
+        p = np.zeros(self.num_params(), np.float32)
+        _check(library().lbm_net_get_params(self.h, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.num_params()
+        _check(library().lbm_net_set_params(self.h, p.ctypes.data))
+
+    def grads(self):
+        p = np.zeros(self.num_params(), np.float32)
+        _check(library().lbm_net_get_grads(self.h, p.ctypes.data))
+        return p
+
+    def forward(self, x):
+        import torch
+        nvol, D, H, W, _ = x.shape
+        z = torch.empty_like(x)
+        _check(library().lbm_net_forward(self.h, _ptr(x), D, H, W, nvol, _ptr(z)))
+        return z
+
+    def predict(self, x, skip=None):
+        import torch
+        nvol, D, H, W, _ = x.shape
+        pred = torch.empty((nvol, D, H, W, self.out_channels), dtype=torch.float32, device=x.device)
+        _check(library().lbm_net_predict(self.h, _ptr(x), _ptr(skip), D, H, W, nvol, _ptr(pred)))
+        return pred
+
+    def gradient(self, target, skip=None, weight=None):
+        """Loss and parameter gradients of the last forward/predict call's input."""
+        loss = ctypes.c_double()
+        _check(library().lbm_net_gradient(self.h, _ptr(skip), _ptr(target), _ptr(weight), ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, target, skip=None, weight=None, lr=1e-3):
+        nvol, D, H, W, _ = x.shape
+        loss = ctypes.c_double()
+        _check(library().lbm_net_train_step(self.h, _ptr(x), _ptr(skip), _ptr(target), _ptr(weight), D, H, W, nvol,
+                                            lr, ctypes.byref(loss)))
+        return loss.value
