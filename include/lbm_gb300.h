@@ -243,6 +243,15 @@ lbm_status lbm_batch_cell_updates_per_coarse_step(const lbm_batch* b, int64_t* n
 lbm_status lbm_batch_launches_per_coarse_step(const lbm_batch* b, int32_t* n);
 lbm_status lbm_batch_destroy(lbm_batch* b);
 
+/* Steady-state residual: r = ||u(t) - u(t')||_2 / ||u(t)||_2 over the owned fluid cells of all
+ * levels, each cell weighted by its volume 8^-L, where u is the velocity of lbm_get_macroscopic,
+ * t the state now and t' the state at the previous call (call it every 10 coarse steps; the flow
+ * counts as steady when r < 1e-6).  The paper defines no residual; this is the reading used for
+ * the warm-start comparison.  The first call on a forest only records u and returns r = HUGE_VAL.
+ * Keeps one velocity copy per level on the device.  Synchronises the stream; LBM_ENONFINITE if a
+ * fluid cell's velocity is not finite (a diverged run). */
+lbm_status lbm_velocity_residual(lbm_forest* f, double* r);
+
 /* ---- learned warm start: a 3-D convolutional net -------------------------------------------
  * The paper has no learned component; this net serves the warm start of the refined levels.  It
  * maps the coarse-only solution, upsampled onto a refined block plus a halo, to the refined
@@ -267,6 +276,33 @@ lbm_status lbm_batch_destroy(lbm_batch* b);
  * 0.999, eps 1e-8) with learning rate lr.  All pointers except the host parameter buffers are
  * device pointers; calls run on `stream` and synchronise it where they return a loss. */
 typedef struct lbm_net lbm_net;
+
+/* Data movement of the warm start (device pointers, asynchronous on `stream`).
+ * lbm_warmstart_features: inputs of the net for the blocks[nblocks][3] (block coordinates) of a
+ * refined level `level` of block size B: one volume of (B + 2 halo)^3 voxels per block.  Each
+ * voxel takes the coarse-only solution sampled trilinearly at its cell centre.  The coarse-only
+ * solution is coarse_rho[n0] and coarse_u[3][n0], a level-0-only forest of coarse_blocks[3] blocks
+ * of the same B, in that forest's block-major order.  Axes in periodic_mask (bit a) wrap, walled
+ * axes clamp; coarse obstacle cells are skipped.  Channels:
+ *   0      (rho - 1) rho_scale
+ *   1..3   u u_scale
+ *   4      1 inside an obstacle sphere (spheres[nspheres][4] = cx, cy, cz, r in level-0 units) or
+ *          outside the domain
+ *   5      level / 2
+ * x is BF16 [nblocks][D][D][D][16]; skip (FP32 [..][4], may be NULL) receives channels 0..3.
+ * lbm_warmstart_targets: a refined level's solution (block-major rho[n], u[3][n], n = nblocks B^3,
+ * as lbm_get_macroscopic returns it) scaled the same way into target FP32 [..][4] on each volume's
+ * interior, with weight 1 on fluid interior voxels and 0 elsewhere.
+ * lbm_warmstart_fields: the inverse map of a prediction FP32 [..][4] to block-major rho[n],
+ * u[3][n] of the interior voxels, ready for lbm_init_equilibrium(on_device = 1). */
+lbm_status lbm_warmstart_features(const double* coarse_rho, const double* coarse_u, const int32_t coarse_blocks[3],
+                                  int32_t B, int32_t periodic_mask, int32_t level, int32_t halo, const int32_t* blocks,
+                                  int32_t nblocks, const double* spheres, int32_t nspheres, double rho_scale,
+                                  double u_scale, void* x, float* skip, void* stream);
+lbm_status lbm_warmstart_targets(const double* rho, const double* u, int32_t B, int32_t halo, int32_t nblocks,
+                                 double rho_scale, double u_scale, float* target, float* weight, void* stream);
+lbm_status lbm_warmstart_fields(const float* pred, int32_t B, int32_t halo, int32_t nblocks, double rho_scale,
+                                double u_scale, double* rho, double* u, void* stream);
 lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_channels, uint64_t seed, void* stream,
                           lbm_net** out);
 lbm_status lbm_net_destroy(lbm_net* n);

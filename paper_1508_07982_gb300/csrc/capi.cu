@@ -81,6 +81,48 @@ __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
     if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
+// Volume-weighted sums {sum w |u - u_prev|^2, sum w |u|^2, fluid cells with a non-finite velocity}
+// over the fluid cells of one level's velocity u[3][n] (cell classes `cell`; obstacle cells hold
+// NaN by design); u_prev takes u.  One partial per CTA.
+__global__ void residual_kernel(const double* __restrict__ u, double* __restrict__ uprev, const uint8_t* __restrict__ cell,
+                                int64_t n, double w, double* __restrict__ partial) {
+    double s0 = 0.0, s1 = 0.0, bad = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        if (cell[i] != CK_FLUID) continue;
+        double d2 = 0.0, u2 = 0.0;
+        bool ok = true;
+        for (int a = 0; a < 3; a++) {
+            const double v = u[a * n + i], p = uprev[a * n + i];
+            ok = ok && isfinite(v);
+            d2 += (v - p) * (v - p);
+            u2 += v * v;
+            uprev[a * n + i] = v;
+        }
+        if (ok) {
+            s0 += w * d2;
+            s1 += w * u2;
+        } else {
+            bad += 1.0;
+        }
+    }
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = bad;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (int(threadIdx.x) < k)
+            for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[4 * blockIdx.x] = red[0][0];
+        partial[4 * blockIdx.x + 1] = red[1][0];
+        partial[4 * blockIdx.x + 2] = red[2][0];
+        partial[4 * blockIdx.x + 3] = 0.0;
+    }
+}
+
 const Launchers& launchers_for(int precision) {
     if (precision == LBM_FP64) return launchers_f64();
     if (precision == LBM_FP32S) return launchers_f32();
@@ -123,6 +165,8 @@ struct lbm_forest {
     int64_t updates = 0;
     int lzc = 3;        // upper bound of log2 cells per thread along z (small levels use fewer)
     int minb = 3;       // CTAs per SM of the step-kernel variant
+    std::vector<double*> uprev;   // per level, the velocity of the previous residual call
+    double* d_rpart = nullptr;    // residual partial sums
 };
 
 namespace {
@@ -366,6 +410,8 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.gwork[1]);
         cudaFree(b.ework);
     }
+    for (double* p : f->uprev) cudaFree(p);
+    cudaFree(f->d_rpart);
     cudaFree(f->d_params);
     cudaFree(f->d_wall);
     cudaFree(f->d_partial);
@@ -676,6 +722,40 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
     for (int k = 0; k < 4; k++) out[k] = f->h_out[k];
     for (int k = 0; k < 4; k++)
         if (!std::isfinite(out[k])) return fail(LBM_ENONFINITE, "non-finite total (component %d)", k);
+    return LBM_OK;
+}
+
+lbm_status lbm_velocity_residual(lbm_forest* f, double* r) {
+    if (!f || !r) return fail(LBM_EINVAL, "NULL argument");
+    if (!f->params_set || f->init_mask != (1u << f->plan.nlev) - 1)
+        return fail(LBM_EINVAL, "set the level parameters and initialise every level first");
+    const Plan& P = f->plan;
+    constexpr int G = 128;
+    if (!f->d_rpart) CU(cudaMalloc(&f->d_rpart, size_t(P.nlev) * G * 4 * sizeof(double)));
+    const bool first = f->uprev.empty();
+    if (first) f->uprev.assign(P.nlev, nullptr);
+    for (int L = 0; L < P.nlev; L++) {
+        const int64_t n = owned_cells(f, L);
+        double* part = f->d_rpart + size_t(L) * G * 4;
+        if (n == 0) {
+            CU(cudaMemsetAsync(part, 0, G * 4 * sizeof(double), f->stream));
+            continue;
+        }
+        lbm_status s = ensure_stage(f, size_t(n) * 4 * sizeof(double));
+        if (s) return s;
+        double* st = static_cast<double*>(f->d_stage);
+        if (!f->uprev[L]) CU(cudaMalloc(&f->uprev[L], size_t(n) * 3 * sizeof(double)));
+        f->L->macro(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, st, st + n, f->stream);
+        residual_kernel<<<G, 256, 0, f->stream>>>(st + n, f->uprev[L], f->dl[L].cell, n, std::ldexp(1.0, -3 * L), part);
+    }
+    reduce_final_kernel<<<1, 256, 0, f->stream>>>(f->d_rpart, P.nlev * G, f->d_out);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(f->h_out, f->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+    CU(cudaStreamSynchronize(f->stream));
+    if (f->h_out[2] > 0.0 || !std::isfinite(f->h_out[0]) || !std::isfinite(f->h_out[1]))
+        return fail(LBM_ENONFINITE, "non-finite velocity in %.0f fluid cells", f->h_out[2]);
+    if (first) *r = HUGE_VAL;
+    else *r = f->h_out[1] > 0.0 ? std::sqrt(f->h_out[0] / f->h_out[1]) : 0.0;
     return LBM_OK;
 }
 

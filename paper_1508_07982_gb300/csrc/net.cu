@@ -512,3 +512,181 @@ lbm_status lbm_net_get_grads(const lbm_net* n, float* host) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- warm-start data movement
+namespace {
+
+// Coarse-only solution on a full level-0 grid of nb[3] blocks of B^3 cells, block-major in the
+// forest's order (block (bx, by, bz) is block (bz nb1 + by) nb0 + bx).  Value of component `comp`
+// of a field [ncomp][n0] at cell (i, j, k), with periodic axes wrapped and walled axes clamped.
+struct Coarse {
+    const double* rho;
+    const double* u;
+    long long n0;
+    int nb[3], B, per;
+    __device__ __forceinline__ int fold(int i, int a) const {
+        const int N = nb[a] * B;
+        if ((per >> a) & 1) return ((i % N) + N) % N;
+        return i < 0 ? 0 : (i >= N ? N - 1 : i);
+    }
+    __device__ __forceinline__ long long index(int i, int j, int k) const {
+        i = fold(i, 0);
+        j = fold(j, 1);
+        k = fold(k, 2);
+        const long long blk = ((long long)(k / B) * nb[1] + j / B) * nb[0] + i / B;
+        return blk * B * B * B + ((long long)(k % B) * B + j % B) * B + i % B;
+    }
+};
+
+// Features of voxel (vx, vy, vz) of the volume around block `blk` of level L: the coarse solution
+// sampled trilinearly at the voxel's cell centre (Sec. 2: cell-centred values), the obstacle /
+// outside-domain flag and the level.
+__global__ void features_kernel(Coarse c, int level, int B, int halo, const int* __restrict__ blocks, int nblocks,
+                                const double* __restrict__ spheres, int nspheres, double rho_scale, double u_scale,
+                                __nv_bfloat16* __restrict__ x, float* __restrict__ skip) {
+    const int D = B + 2 * halo;
+    const long long V = (long long)D * D * D;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nblocks) return;
+    const int b = int(id / V);
+    long long r = id - b * V;
+    const int vx = int(r % D);
+    r /= D;
+    const int vy = int(r % D), vz = int(r / D);
+    const int g[3] = {blocks[3 * b] * B + vx - halo, blocks[3 * b + 1] * B + vy - halo, blocks[3 * b + 2] * B + vz - halo};
+    const double s = 1.0 / double(1 << level);
+    double p[3];
+    bool outside = false;
+    for (int a = 0; a < 3; a++) {
+        p[a] = (g[a] + 0.5) * s;   // level-0 units
+        if (!((c.per >> a) & 1) && (p[a] < 0.0 || p[a] >= double(c.nb[a] * c.B))) outside = true;
+    }
+    bool solid = outside;
+    for (int i = 0; i < nspheres && !solid; i++) {
+        const double* q = spheres + 4 * i;
+        const double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+        solid = dx * dx + dy * dy + dz * dz < q[3] * q[3];
+    }
+    int i0[3];
+    double w[3];
+    for (int a = 0; a < 3; a++) {
+        const double t = p[a] - 0.5;
+        const double f = floor(t);
+        i0[a] = int(f);
+        w[a] = t - f;
+    }
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int corner = 0; corner < 8; corner++) {
+        const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+        const double wt = (dx ? w[0] : 1.0 - w[0]) * (dy ? w[1] : 1.0 - w[1]) * (dz ? w[2] : 1.0 - w[2]);
+        const long long k = c.index(i0[0] + dx, i0[1] + dy, i0[2] + dz);
+        const double rho = c.rho[k];
+        if (!isfinite(rho)) continue;   // obstacle cells of the coarse solution hold no value
+        v[0] += wt * (rho - 1.0);
+        for (int a = 0; a < 3; a++) v[1 + a] += wt * c.u[a * c.n0 + k];
+    }
+    __nv_bfloat16* xo = x + id * CH;
+    const float f0 = float(v[0] * rho_scale), f1 = float(v[1] * u_scale), f2 = float(v[2] * u_scale),
+                f3 = float(v[3] * u_scale);
+    const float vals[CH] = {f0, f1, f2, f3, solid ? 1.f : 0.f, float(level) * 0.5f};
+    for (int ch = 0; ch < CH; ch++) xo[ch] = __float2bfloat16_rn(vals[ch]);
+    if (skip) {
+        skip[id * 4 + 0] = f0;
+        skip[id * 4 + 1] = f1;
+        skip[id * 4 + 2] = f2;
+        skip[id * 4 + 3] = f3;
+    }
+}
+
+// Refined solution (block-major rho[n], u[3][n] of one level) -> training targets on the interior
+// of each volume; weight 1 there on fluid cells, 0 on the halo and on obstacle cells.
+__global__ void targets_kernel(const double* __restrict__ rho, const double* __restrict__ u, long long n, int B, int halo,
+                               int nblocks, double rho_scale, double u_scale, float* __restrict__ target,
+                               float* __restrict__ weight) {
+    const int D = B + 2 * halo;
+    const long long V = (long long)D * D * D;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= V * nblocks) return;
+    const int b = int(id / V);
+    long long r = id - b * V;
+    const int vx = int(r % D) - halo;
+    r /= D;
+    const int vy = int(r % D) - halo, vz = int(r / D) - halo;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    float w = 0.f;
+    if (vx >= 0 && vx < B && vy >= 0 && vy < B && vz >= 0 && vz < B) {
+        const long long k = (long long)b * B * B * B + ((long long)vz * B + vy) * B + vx;
+        if (isfinite(rho[k])) {
+            t[0] = float((rho[k] - 1.0) * rho_scale);
+            for (int a = 0; a < 3; a++) t[1 + a] = float(u[a * n + k] * u_scale);
+            w = 1.f;
+        }
+    }
+    for (int a = 0; a < 4; a++) target[id * 4 + a] = t[a];
+    weight[id] = w;
+}
+
+// Prediction on the interior of each volume -> block-major rho[n], u[3][n] of one level.
+__global__ void fields_kernel(const float* __restrict__ pred, int B, int halo, int nblocks, double rho_scale,
+                              double u_scale, double* __restrict__ rho, double* __restrict__ u) {
+    const long long n = (long long)nblocks * B * B * B;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int b = int(k / ((long long)B * B * B));
+    long long r = k - (long long)b * B * B * B;
+    const int x = int(r % B);
+    r /= B;
+    const int y = int(r % B), z = int(r / B);
+    const int D = B + 2 * halo;
+    const long long id = (long long)b * D * D * D + ((long long)(z + halo) * D + (y + halo)) * D + (x + halo);
+    rho[k] = 1.0 + double(pred[id * 4]) / rho_scale;
+    for (int a = 0; a < 3; a++) u[a * n + k] = double(pred[id * 4 + 1 + a]) / u_scale;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_warmstart_features(const double* coarse_rho, const double* coarse_u, const int32_t coarse_blocks[3],
+                                  int32_t B, int32_t periodic_mask, int32_t level, int32_t halo, const int32_t* blocks,
+                                  int32_t nblocks, const double* spheres, int32_t nspheres, double rho_scale,
+                                  double u_scale, void* x, float* skip, void* stream) {
+    if (!coarse_rho || !coarse_u || !coarse_blocks || !blocks || !x || (nspheres > 0 && !spheres))
+        return nfail(LBM_EINVAL, "NULL argument");
+    if (B < 1 || halo < 0 || level < 0 || level > 20 || nblocks < 0 || nspheres < 0)
+        return nfail(LBM_EINVAL, "invalid sizes");
+    if (nblocks == 0) return LBM_OK;
+    Coarse c{coarse_rho, coarse_u, 0, {coarse_blocks[0], coarse_blocks[1], coarse_blocks[2]}, B, periodic_mask};
+    c.n0 = (long long)c.nb[0] * c.nb[1] * c.nb[2] * B * B * B;
+    const long long D = B + 2 * halo, total = D * D * D * nblocks;
+    features_kernel<<<unsigned((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        c, level, B, halo, blocks, nblocks, spheres, nspheres, rho_scale, u_scale, static_cast<__nv_bfloat16*>(x), skip);
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_warmstart_targets(const double* rho, const double* u, int32_t B, int32_t halo, int32_t nblocks,
+                                 double rho_scale, double u_scale, float* target, float* weight, void* stream) {
+    if (!rho || !u || !target || !weight) return nfail(LBM_EINVAL, "NULL argument");
+    if (B < 1 || halo < 0 || nblocks < 0) return nfail(LBM_EINVAL, "invalid sizes");
+    if (nblocks == 0) return LBM_OK;
+    const long long D = B + 2 * halo, total = D * D * D * nblocks, n = (long long)nblocks * B * B * B;
+    targets_kernel<<<unsigned((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        rho, u, n, B, halo, nblocks, rho_scale, u_scale, target, weight);
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_warmstart_fields(const float* pred, int32_t B, int32_t halo, int32_t nblocks, double rho_scale,
+                                double u_scale, double* rho, double* u, void* stream) {
+    if (!pred || !rho || !u) return nfail(LBM_EINVAL, "NULL argument");
+    if (B < 1 || halo < 0 || nblocks < 0) return nfail(LBM_EINVAL, "invalid sizes");
+    if (nblocks == 0) return LBM_OK;
+    const long long n = (long long)nblocks * B * B * B;
+    fields_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, B, halo, nblocks,
+                                                                                          rho_scale, u_scale, rho, u);
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+}  // extern "C"

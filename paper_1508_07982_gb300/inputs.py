@@ -90,6 +90,37 @@ def batch_cases(n=256, seed=SEED, B=16):
     return cases
 
 
+def warm_cases(n, seed=SEED, H=128, B=16, u_in=0.04, re_range=(20.0, 60.0)):
+    """Channels H x H x H past 1-5 spheres, refined twice around them (the warm-start workload).
+
+    Per case: sphere count uniform in 1..5, radii U(0.05, 0.15) H, centres uniform in the middle
+    80 % of the box; Re uniform in re_range on the mean sphere diameter D (nu0 = u_in D / Re).
+    No-slip walls at y = 0 and y = H, periodic x and z, driven by the body force a0 = 12 nu0 u_in
+    / H^2 along x, whose plane Poiseuille flow has mean velocity u_in; TRT with Lambda = 3/16.
+    Level 1 covers balls of radius r + H/16, level 2 balls of radius r + 3H/128 (level-0 units)
+    around each sphere.
+    """
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(n):
+        k = int(rng.integers(1, 6))
+        radii = rng.uniform(0.05, 0.15, k) * H
+        centres = rng.uniform(0.1 * H, 0.9 * H, (k, 3))
+        re = float(rng.uniform(*re_range))
+        nu0 = u_in * 2.0 * float(radii.mean()) / re
+        regions = [("ball", 1, tuple(float(v) for v in c), float(r) + H / 16.0) for c, r in zip(centres, radii)]
+        regions += [("ball", 2, tuple(float(v) for v in c), float(r) + 3.0 * H / 128.0) for c, r in zip(centres, radii)]
+        r0 = H // B
+        cases.append(dict(root=(r0, r0, r0), B=B, lmax=2, collision="trt", rho0=1.0,
+                          bc=["periodic", "periodic", "noslip", "noslip", "periodic", "periodic"],
+                          bc_u=[(0.0, 0.0, 0.0)] * 6,
+                          spheres=[tuple(float(v) for v in c) + (float(r),) for c, r in zip(centres, radii)],
+                          regions=regions, lambda_e0=1.0 / (3.0 * nu0 + 0.5), magic=3.0 / 16.0,
+                          accel=(12.0 * nu0 * u_in / H ** 2, 0.0, 0.0), u_init=(0.0, 0.0, 0.0), re=re,
+                          u_in=u_in))
+    return cases
+
+
 def periodic_case(n=64, B=16, collision="srt", omega=1.9, regions=(), lmax=0):
     """Fully periodic cube of n^3 level-0 cells (uniform unless regions refine it)."""
     r = n // B

@@ -32,7 +32,8 @@ EXPORTS = [
     "lbm_batch_set_kernel_config", "lbm_batch_autotune", "lbm_batch_cell_updates_per_coarse_step",
     "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_num_params", "lbm_net_get_params", "lbm_net_set_params", "lbm_net_forward", "lbm_net_predict",
-    "lbm_net_gradient", "lbm_net_get_grads", "lbm_net_train_step",
+    "lbm_net_gradient", "lbm_net_get_grads", "lbm_net_train_step", "lbm_velocity_residual",
+    "lbm_warmstart_features", "lbm_warmstart_targets", "lbm_warmstart_fields",
 ]
 NOALLOC_MAX_CELLS = 16384 * 4096
 
@@ -125,6 +126,13 @@ def library():
             "lbm_net_get_grads": [P, P],
             "lbm_net_train_step": [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_float, dp],
+            "lbm_velocity_residual": [P, dp],
+            "lbm_warmstart_features": [P, P, i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, P, P, P],
+            "lbm_warmstart_targets": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_double, P, P, P],
+            "lbm_warmstart_fields": [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.c_double, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -365,6 +373,12 @@ class Forest:
         _check(library().lbm_get_macroscopic(self.h, level, _ptr(rho), _ptr(u), 1 if on_device else 0))
         return rho, u
 
+    def velocity_residual(self):
+        """lbm_velocity_residual: relative velocity change since the previous call (inf first)."""
+        r = ctypes.c_double()
+        _check(library().lbm_velocity_residual(self.h, ctypes.byref(r)))
+        return r.value
+
     def get_pdfs(self, level, out=None, on_device=False):
         if on_device:
             _check(library().lbm_get_pdfs(self.h, level, _ptr(out), 1))
@@ -530,3 +544,44 @@ class Net:
         _check(library().lbm_net_train_step(self.h, _ptr(x), _ptr(skip), _ptr(target), _ptr(weight), D, H, W, nvol,
                                             lr, ctypes.byref(loss)))
         return loss.value
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def warmstart_features(coarse_rho, coarse_u, coarse_blocks, B, periodic_mask, level, halo, blocks, spheres,
+                       rho_scale, u_scale):
+    """lbm_warmstart_features on device tensors; returns (x BF16 [n, D, D, D, 16], skip FP32 [.., 4])."""
+    import torch
+    nb = blocks.shape[0]
+    D = B + 2 * halo
+    x = torch.empty((nb, D, D, D, 16), dtype=torch.bfloat16, device="cuda")
+    skip = torch.empty((nb, D, D, D, 4), dtype=torch.float32, device="cuda")
+    cb = np.ascontiguousarray(coarse_blocks, np.int32)
+    ns = 0 if spheres is None else int(spheres.shape[0])
+    _check(library().lbm_warmstart_features(_ptr(coarse_rho), _ptr(coarse_u), cb.ctypes.data_as(
+        ctypes.POINTER(ctypes.c_int32)), B, periodic_mask, level, halo, _ptr(blocks), nb, _ptr(spheres), ns,
+        rho_scale, u_scale, _ptr(x), _ptr(skip), _stream()))
+    return x, skip
+
+
+def warmstart_targets(rho, u, B, halo, nblocks, rho_scale, u_scale):
+    import torch
+    D = B + 2 * halo
+    target = torch.empty((nblocks, D, D, D, 4), dtype=torch.float32, device="cuda")
+    weight = torch.empty((nblocks, D, D, D), dtype=torch.float32, device="cuda")
+    _check(library().lbm_warmstart_targets(_ptr(rho), _ptr(u), B, halo, nblocks, rho_scale, u_scale, _ptr(target),
+                                           _ptr(weight), _stream()))
+    return target, weight
+
+
+def warmstart_fields(pred, B, halo, nblocks, rho_scale, u_scale):
+    import torch
+    n = nblocks * B ** 3
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    u = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    _check(library().lbm_warmstart_fields(_ptr(pred), B, halo, nblocks, rho_scale, u_scale, _ptr(rho), _ptr(u),
+                                          _stream()))
+    return rho, u
