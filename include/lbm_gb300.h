@@ -316,6 +316,12 @@ lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, 
 lbm_status lbm_net_get_grads(const lbm_net* n, float* host);
 lbm_status lbm_net_train_step(lbm_net* n, const void* x, const float* skip, const float* target, const float* weight,
                               int32_t D, int32_t H, int32_t W, int32_t nvol, float lr, double* loss);
+/* Tensor-core path of the convolutions: 1 (default) runs them with tcgen05.mma into TMEM where
+ * a volume's zero-padded planes fit in shared memory (W, H up to about 40), 0 with warp-level
+ * mma.sync everywhere.  Both compute the same products in BF16 x BF16 -> FP32; the sums are
+ * ordered differently.  Calls that wait on the tcgen05 kernel return LBM_ETIMEOUT if one of its
+ * bounded waits ran out. */
+lbm_status lbm_net_set_backend(lbm_net* n, int32_t backend);
 
 /* ---- totals without allocation ------------------------------------------------------------
  * The paper has no counterpart: this entry point serves callers that cannot allocate device

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -102,6 +103,144 @@ __global__ void __launch_bounds__(256) conv_kernel(const __nv_bfloat16* __restri
             }
             reinterpret_cast<__nv_bfloat162*>(Z)[v * (CH / 2) + n / 2] = __floats2bfloat162_rn(z0, z1);
         }
+}
+
+// ---------------------------------------------------------------- tcgen05 convolution
+// The same product as conv_kernel on the 5th-generation tensor cores.  One CTA (4 warps) walks
+// (volume, z-plane) units.  For a unit it stages the input planes z-1, z, z+1 in shared memory as
+// zero-padded (H + 2) x P slots (P = W + 2), in two halves of 8 channels: half c of slot s at
+// byte 16 (c NSL + s) of its plane.  In this K-major, unswizzled layout the A operand of tap
+// (dx, dy, dz) for 128 consecutive output slots s0.. is the same window shifted by dy P + dx slots
+// in plane dz + 1, so each tap is one M128 N16 K16 BF16 MMA (tcgen05.mma kind::f16, FP32
+// accumulator in TMEM) whose descriptor differs only in its start address; 27 of them accumulate
+// a tile.  One thread issues them and commits to an mbarrier; the 4 warps then read their 32 TMEM
+// lanes (tcgen05.ld 32x32b.x16: one output slot's 16 channels per thread), keep interior slots,
+// and apply bias and activation as conv_kernel does.
+constexpr int TC_W_BYTES = TAPS * 2 * CH * 8 * 2;   // weights [tap][half][n][8] BF16
+constexpr int TC_A_OFF = 14336;                     // after the weights, barrier and TMEM slot
+constexpr int TC_BAR_OFF = TC_W_BYTES;
+constexpr int TC_TM_OFF = TC_W_BYTES + 8;
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    // start address, leading byte offset (K direction), stride byte offset (M/N direction), all in
+    // 16-byte units; bit 46: descriptor version of tcgen05; no swizzle, base offset 0
+    return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+__global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
+                                                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ Z, Dims d,
+                                                      int act, const __nv_bfloat16* __restrict__ mask, int P, int NSL,
+                                                      int ntile, int tmcols, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(sm));
+    const uint32_t bar = base + TC_BAR_OFF, wbase = base, abase = base + TC_A_OFF;
+    // weights: Wt[o][n][k] -> [o][k / 8][n][k % 8]
+    for (int i = tid; i < TAPS * CH * CH; i += blockDim.x) {
+        const int o = i / (CH * CH), n = (i / CH) % CH, k = i % CH;
+        reinterpret_cast<__nv_bfloat16*>(sm)[((o * 2 + k / 8) * CH + n) * 8 + k % 8] = Wt[i];
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + TC_TM_OFF), "r"(tmcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TC_TM_OFF);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+    const int H = d.H, W = d.W, D = d.D;
+    const int plane_slots = (H + 2) * P;
+    uint32_t phase = 0;
+    for (long long unit = blockIdx.x; unit < (long long)d.nvol * D; unit += gridDim.x) {
+        const long long vol = unit / D;
+        const int z = int(unit - vol * D);
+        // stage the three input planes, zero-padded
+        for (int p = 0; p < 3; p++) {
+            const int zz = z + p - 1;
+            const bool pv = zz >= 0 && zz < D;
+            for (int idx = tid; idx < NSL * 2; idx += blockDim.x) {
+                const int slot = idx >> 1, c = idx & 1;
+                const int y = slot / P, x = slot - (slot / P) * P;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (pv && slot < plane_slots && y >= 1 && y <= H && x >= 1 && x <= W) {
+                    const long long vox = ((vol * D + zz) * H + (y - 1)) * W + (x - 1);
+                    v = __ldg(reinterpret_cast<const uint4*>(X + vox * CH) + c);
+                }
+                *reinterpret_cast<uint4*>(sm + TC_A_OFF + ((p * 2 + c) * NSL + slot) * 16) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int t = 0; t < ntile; t++) {
+                const int s0 = P + 1 + 128 * t;
+                for (int o = 0; o < TAPS; o++) {
+                    const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+                    const uint32_t a = abase + uint32_t(((dz + 1) * 2 * NSL + s0 + dy * P + dx) * 16);
+                    const uint64_t ad = smem_desc(a, uint32_t(NSL * 16), 128u);
+                    const uint64_t bd = smem_desc(wbase + uint32_t(o * 2 * CH * 8 * 2), uint32_t(CH * 16), 128u);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + uint32_t(t * 16)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(o));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+        }
+        // bounded wait for this unit's products
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 24) && !done; it++)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+        phase ^= 1u;
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int t = 0; t < ntile; t++) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(tmem + (uint32_t(warp * 32) << 16) + uint32_t(t * 16)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int s = P + 1 + 128 * t + warp * 32 + lane;
+            const int y = s / P, x = s - (s / P) * P;
+            if (y < 1 || y > H || x < 1 || x > W) continue;
+            const long long v = ((vol * D + z) * H + (y - 1)) * W + (x - 1);
+            __nv_bfloat162 o2[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                float z0 = __uint_as_float(r[2 * c]) + (bias ? bias[2 * c] : 0.f);
+                float z1 = __uint_as_float(r[2 * c + 1]) + (bias ? bias[2 * c + 1] : 0.f);
+                if (act == 1) {
+                    z0 = fmaxf(z0, 0.f);
+                    z1 = fmaxf(z1, 0.f);
+                } else if (act == 2) {
+                    const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mask)[v * (CH / 2) + c];
+                    if (!(__bfloat162float(m.x) > 0.f)) z0 = 0.f;
+                    if (!(__bfloat162float(m.y) > 0.f)) z1 = 0.f;
+                }
+                o2[c] = __floats2bfloat162_rn(z0, z1);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(Z + v * CH);
+            dst[0] = *reinterpret_cast<uint4*>(&o2[0]);
+            dst[1] = *reinterpret_cast<uint4*>(&o2[4]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmcols) : "memory");
 }
 
 // dW[o][m][n] += sum_v dZ[v][m] X[v + o][n] and db[m] += sum_v dZ[v][m].  Block (chunk, o): 8 warps,
@@ -271,6 +410,9 @@ struct lbm_net {
     long long cap = 0;       // voxels the activation buffers hold
     double* d_loss = nullptr;
     double* h_loss = nullptr;
+    int* d_err = nullptr;    // set by the tcgen05 kernel if a wait ran out
+    int backend = 1;         // 1: tcgen05 products where the volume fits, 0: mma.sync only
+    int sms = 0;
     Dims d{};
 };
 
@@ -302,6 +444,57 @@ lbm_status ensure_acts(lbm_net* n, long long N) {
     return LBM_OK;
 }
 
+// Shared-memory and TMEM geometry of conv_tc_kernel for a volume; false if it does not fit.
+struct TcGeom {
+    int P, NSL, ntile, tmcols, per_sm;
+    size_t smem;
+};
+
+bool tc_geometry(const Dims& d, TcGeom& g) {
+    g.P = d.W + 2;
+    g.NSL = (((d.H + 2) * g.P + 160) + 7) & ~7;
+    g.ntile = (d.H * g.P + 127) / 128;
+    g.tmcols = 32;
+    while (g.tmcols < g.ntile * 16) g.tmcols *= 2;
+    g.smem = size_t(TC_A_OFF) + size_t(6) * g.NSL * 16;
+    if (g.tmcols > 512 || g.smem > 227 * 1024) return false;
+    g.per_sm = int(std::min<size_t>(std::min<size_t>(228 * 1024 / (g.smem + 1024), 512 / g.tmcols), 16));
+    return g.per_sm >= 1;
+}
+
+// Z = conv(X) (+ bias, activation) with the tensor-core kernel the net is set to use.
+lbm_status conv(lbm_net* n, const __nv_bfloat16* X, const __nv_bfloat16* Wt, const float* bias, __nv_bfloat16* Z,
+                const Dims& d, int act, const __nv_bfloat16* mask) {
+    TcGeom g;
+    if (n->backend == 1 && tc_geometry(d, g)) {
+        static size_t attr_smem = 0;
+        if (g.smem > attr_smem) {
+            NCU(cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)));
+            attr_smem = g.smem;
+        }
+        const long long units = (long long)d.nvol * d.D;
+        const int grid = int(std::min<long long>(units, (long long)n->sms * g.per_sm));
+        conv_tc_kernel<<<grid, 128, g.smem, n->stream>>>(X, Wt, bias, Z, d, act, mask, g.P, g.NSL, g.ntile, g.tmcols,
+                                                        n->d_err);
+    } else {
+        conv_kernel<<<int((d.N + 127) / 128), 256, 0, n->stream>>>(X, Wt, bias, Z, d, act, mask);
+    }
+    NCU(cudaGetLastError());
+    return LBM_OK;
+}
+
+// LBM_ETIMEOUT if a tcgen05 wait ran out since the last check (synchronises the stream).
+lbm_status check_err(lbm_net* n) {
+    int e = 0;
+    NCU(cudaMemcpyAsync(&e, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NCU(cudaStreamSynchronize(n->stream));
+    if (e) {
+        NCU(cudaMemset(n->d_err, 0, sizeof(int)));
+        return nfail(LBM_ETIMEOUT, "a tensor-core wait ran out; the outputs of this call are incomplete");
+    }
+    return LBM_OK;
+}
+
 lbm_status refresh_weights(lbm_net* n) {
     for (int l = 0; l < n->layers; l++)
         weights_kernel<<<(TAPS * CH * CH + 255) / 256, 256, 0, n->stream>>>(
@@ -327,13 +520,12 @@ lbm_status forward(lbm_net* n, const __nv_bfloat16* x, const Dims& d) {
     lbm_status s = ensure_acts(n, d.N);
     if (s) return s;
     NCU(cudaMemcpyAsync(n->act[0], x, size_t(d.N) * CH * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice, n->stream));
-    const int grid = int((d.N + 127) / 128);
     for (int l = 0; l < n->layers; l++) {
         const float* b = n->params + size_t(l) * PER_LAYER + TAPS * CH * CH;
-        conv_kernel<<<grid, 256, 0, n->stream>>>(n->act[l], n->wf + size_t(l) * TAPS * CH * CH, b, n->act[l + 1], d,
-                                                 l + 1 < n->layers ? 1 : 0, nullptr);
+        lbm_status st = conv(n, n->act[l], n->wf + size_t(l) * TAPS * CH * CH, b, n->act[l + 1], d,
+                             l + 1 < n->layers ? 1 : 0, nullptr);
+        if (st) return st;
     }
-    NCU(cudaGetLastError());
     n->d = d;
     return LBM_OK;
 }
@@ -379,11 +571,16 @@ lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_chann
         cudaMalloc(&n->m, np * 4) != cudaSuccess || cudaMalloc(&n->v, np * 4) != cudaSuccess ||
         cudaMalloc(&n->wf, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
         cudaMalloc(&n->wb, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
-        cudaMalloc(&n->d_loss, sizeof(double)) != cudaSuccess || cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess)
+        cudaMalloc(&n->d_loss, sizeof(double)) != cudaSuccess || cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess)
         return bail(nfail(LBM_ENOMEM, "cannot allocate the net"));
     if (cudaMemcpy(n->params, h.data(), np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(n->m, 0, np * 4) != cudaSuccess || cudaMemset(n->v, 0, np * 4) != cudaSuccess)
+        cudaMemset(n->m, 0, np * 4) != cudaSuccess || cudaMemset(n->v, 0, np * 4) != cudaSuccess ||
+        cudaMemset(n->d_err, 0, sizeof(int)) != cudaSuccess)
         return bail(nfail(LBM_ECUDA, "cannot initialise the net"));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(nfail(LBM_ECUDA, "no CUDA device"));
     lbm_status s = refresh_weights(n);
     if (s) return bail(s);
     *out = n;
@@ -401,6 +598,7 @@ lbm_status lbm_net_destroy(lbm_net* n) {
     cudaFree(n->wf);
     cudaFree(n->wb);
     cudaFree(n->d_loss);
+    cudaFree(n->d_err);
     if (n->h_loss) cudaFreeHost(n->h_loss);
     delete n;
     return LBM_OK;
@@ -432,7 +630,7 @@ lbm_status lbm_net_forward(lbm_net* n, const void* x, int32_t D, int32_t H, int3
     lbm_status s = check_dims(D, H, W, nvol, d);
     if (s || (s = forward(n, static_cast<const __nv_bfloat16*>(x), d))) return s;
     NCU(cudaMemcpyAsync(z, n->act[n->layers], size_t(d.N) * CH * 2, cudaMemcpyDeviceToDevice, n->stream));
-    return LBM_OK;
+    return check_err(n);
 }
 
 lbm_status lbm_net_predict(lbm_net* n, const void* x, const float* skip, int32_t D, int32_t H, int32_t W, int32_t nvol,
@@ -444,7 +642,7 @@ lbm_status lbm_net_predict(lbm_net* n, const void* x, const float* skip, int32_t
     loss_kernel<<<int((d.N + 255) / 256), 256, 0, n->stream>>>(n->act[n->layers], skip, nullptr, nullptr, d.N, n->cout,
                                                                0.f, nullptr, pred, nullptr);
     NCU(cudaGetLastError());
-    return LBM_OK;
+    return check_err(n);
 }
 
 lbm_status lbm_net_train_step(lbm_net* n, const void* x, const float* skip, const float* target, const float* weight,
@@ -484,7 +682,6 @@ lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, 
     NCU(cudaMemsetAsync(n->grads, 0, size_t(n->layers) * PER_LAYER * 4, n->stream));
     loss_kernel<<<int((d.N + 255) / 256), 256, 0, n->stream>>>(n->act[n->layers], skip, target, weight, d.N, n->cout,
                                                                float(1.0 / count), n->g0, nullptr, n->d_loss);
-    const int grid = int((d.N + 127) / 128);
     const long long chunk = 4096;
     const dim3 wg(unsigned((d.N + chunk - 1) / chunk), TAPS);
     __nv_bfloat16* dz = n->g0;
@@ -493,7 +690,8 @@ lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, 
         float* gw = n->grads + size_t(l) * PER_LAYER;
         wgrad_kernel<<<wg, 256, 0, n->stream>>>(n->act[l], dz, gw, gw + TAPS * CH * CH, d, chunk);
         if (l > 0) {
-            conv_kernel<<<grid, 256, 0, n->stream>>>(dz, n->wb + size_t(l) * TAPS * CH * CH, nullptr, dx, d, 2, n->act[l]);
+            lbm_status st = conv(n, dz, n->wb + size_t(l) * TAPS * CH * CH, nullptr, dx, d, 2, n->act[l]);
+            if (st) return st;
             std::swap(dz, dx);
         }
     }
@@ -501,6 +699,12 @@ lbm_status lbm_net_gradient(lbm_net* n, const float* skip, const float* target, 
     NCU(cudaMemcpyAsync(n->h_loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     NCU(cudaStreamSynchronize(n->stream));
     if (loss) *loss = *n->h_loss / count;
+    return check_err(n);
+}
+
+lbm_status lbm_net_set_backend(lbm_net* n, int32_t backend) {
+    if (!n || (backend != 0 && backend != 1)) return nfail(LBM_EINVAL, "backend must be 0 (mma.sync) or 1 (tcgen05)");
+    n->backend = backend;
     return LBM_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_num_params", "lbm_net_get_params", "lbm_net_set_params", "lbm_net_forward", "lbm_net_predict",
     "lbm_net_gradient", "lbm_net_get_grads", "lbm_net_train_step", "lbm_velocity_residual",
-    "lbm_warmstart_features", "lbm_warmstart_targets", "lbm_warmstart_fields",
+    "lbm_warmstart_features", "lbm_warmstart_targets", "lbm_warmstart_fields", "lbm_net_set_backend",
 ]
 NOALLOC_MAX_CELLS = 16384 * 4096
 
@@ -127,6 +127,7 @@ def library():
             "lbm_net_train_step": [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_float, dp],
             "lbm_velocity_residual": [P, dp],
+            "lbm_net_set_backend": [P, ctypes.c_int32],
             "lbm_warmstart_features": [P, P, i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, P, P, P],
             "lbm_warmstart_targets": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -497,6 +498,10 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def set_backend(self, backend):
+        """"tcgen05" (default) or "mma.sync" for the convolutions."""
+        _check(library().lbm_net_set_backend(self.h, {"mma.sync": 0, "tcgen05": 1}[backend]))
 
     def num_params(self):
         n = ctypes.c_int64()

@@ -131,11 +131,13 @@ def _dev(a, dtype):
 
 
 @pytest.mark.gpu
-def test_net_forward_matches_the_oracle(lbm):
+@pytest.mark.parametrize("backend", ["tcgen05", "mma.sync"])
+def test_net_forward_matches_the_oracle(lbm, backend):
     import torch
     rng = _rng(6)
     layers, cin, cout = 5, 6, 4
     net = lbm.Net(layers, cin, cout, seed=1)
+    net.set_backend(backend)
     p = _params(rng, layers, cin, cout)
     p_b = p.copy()
     for l in range(layers):                       # BF16-representable weights
@@ -151,12 +153,14 @@ def test_net_forward_matches_the_oracle(lbm):
 
 
 @pytest.mark.gpu
-def test_net_gradients_match_the_oracle(lbm):
+@pytest.mark.parametrize("backend", ["tcgen05", "mma.sync"])
+def test_net_gradients_match_the_oracle(lbm, backend):
     import torch
     rng = _rng(7)
     layers, cin, cout = 5, 6, 4
     shape = (3, 6, 5, 9)
     net = lbm.Net(layers, cin, cout, seed=2)
+    net.set_backend(backend)
     p = _params(rng, layers, cin, cout)
     for l in range(layers):
         s = slice(l * O.PER_LAYER, l * O.PER_LAYER + O.TAPS * O.CH * O.CH)
@@ -175,6 +179,26 @@ def test_net_gradients_match_the_oracle(lbm):
     assert abs(loss - rl) <= 1e-2 * rl
     assert np.abs(g - rg).max() <= 2e-2 * np.abs(rg).max()
     net.close()
+
+
+@pytest.mark.gpu
+def test_tensor_core_paths_agree_on_a_block_volume(lbm):
+    """The tcgen05 and mma.sync products on an 18^3 volume (a block of 8^3 with its halo of 5):
+    several tiles per plane, and planes at the volume's z faces."""
+    import torch
+    rng = _rng(9)
+    layers, cin, cout = 5, 6, 4
+    p = _params(rng, layers, cin, cout)
+    x = _dev(O.bf16(_input(rng, (3, 18, 18, 18), cin)), torch.bfloat16)
+    out = {}
+    for backend in ("tcgen05", "mma.sync"):
+        net = lbm.Net(layers, cin, cout, seed=4)
+        net.set_backend(backend)
+        net.set_params(p)
+        out[backend] = net.forward(x).float().cpu().numpy()
+        net.close()
+    a, b = out["tcgen05"], out["mma.sync"]
+    assert np.abs(a - b).max() <= 2.0 ** -6 * np.abs(b).max()
 
 
 @pytest.mark.gpu

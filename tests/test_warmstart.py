@@ -52,7 +52,9 @@ def test_features_reproduce_constant_and_linear_coarse_fields(lbm):
     import torch
     from paper_1508_07982_gb300 import warmstart as ws
     with_spheres = _case()
-    case = dict(with_spheres, spheres=[])      # obstacle cells would drop out of the interpolation
+    # no obstacles (their cells drop out of the interpolation) and no body force (the macroscopic
+    # velocity of a forced state includes a/2)
+    case = dict(with_spheres, spheres=[], accel=(0.0, 0.0, 0.0))
     coarse = lbm.Forest(ws.coarse_case(case), precision="fp64")
     fine = lbm.Forest(case, precision="fp64")
     n0 = coarse.n_cells(0)
