@@ -46,6 +46,7 @@ def _args():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-forest leg")
+    p.add_argument("--no-net", action="store_true", help="skip the warm-start net leg")
     return p.parse_args()
 
 
@@ -66,7 +67,7 @@ def _measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return json.load(fh), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
 class ClockSampler:
@@ -324,6 +325,47 @@ def _batch(lbm, torch, steps=500, warmup=5, serial_steps=50):
     return out
 
 
+def _net(lbm, torch, peaks, peak_kind, reps=10):
+    """The warm-start net on 512 volumes of 18^3 voxels (8^3 blocks with a halo of 5): forward
+    passes and training steps, each on the tcgen05 and the mma.sync tensor-core paths.  FLOPs count
+    the 27 x 16 x 16 multiply-adds per voxel and layer that the kernels issue."""
+    shape = (512, 18, 18, 18)
+    n = int(np.prod(shape))
+    x = torch.zeros(shape + (16,), dtype=torch.bfloat16, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(20150827)
+    x[..., :6] = torch.randn(shape + (6,), device="cuda", generator=g).to(torch.bfloat16)
+    target = torch.randn(shape + (4,), device="cuda", generator=g) * 0.1
+    out = {"workload": "512 volumes of 18^3 voxels x 16 channels, 5 layers of 3^3 convolutions, width 16"}
+    stream = torch.cuda.current_stream()
+    for backend in ("tcgen05", "mma.sync"):
+        net = lbm.Net(5, 6, 4, seed=1)
+        net.set_backend(backend)
+        res = {}
+        for kind, fn, flop_layers in (("forward", lambda: net.forward(x), 5),
+                                      ("train_step", lambda: net.train_step(x, target, lr=1e-4), 5 + 4 + 5)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flops = flop_layers * 2 * 27 * 16 * 16 * n
+            res[kind] = {"ms": round(ms, 4), "TFLOPs": round(flops / ms / 1e9, 1)}
+        net.close()
+        out[backend] = res
+    peak = float(peaks["bf16_tflops"])
+    ach = out["tcgen05"]["forward"]["TFLOPs"]
+    out["roofline"] = {"bound": "tensor", "kernel": "conv_tc_kernel (net forward, 5 layers)", "achieved": ach,
+                       "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                       "peak_source": "%s bf16_tflops (MEASURED_PEAKS.json)" % peak_kind}
+    return out
+
+
 def run_reference(args, case):
     """The plain CPU oracle as the reference arm: each timed step is one full coarse step."""
     from oracle import oracle
@@ -424,6 +466,7 @@ def main():
 
     e2e = _e2e(lbm, torch, case, args.precision, min(args.steps, 200)) if rank == 0 and not args.no_e2e else None
     batch = _batch(lbm, torch) if rank == 0 and not args.no_batch else None
+    net = _net(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_net else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(case)
@@ -437,6 +480,8 @@ def main():
         line["precisions"] = variants
     if batch:
         line["batch"] = batch
+    if net:
+        line["warm_start_net"] = net
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()
