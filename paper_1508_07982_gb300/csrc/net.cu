@@ -158,37 +158,47 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
     for (long long unit = blockIdx.x; unit < (long long)d.nvol * D; unit += gridDim.x) {
         const long long vol = unit / D;
         const int z = int(unit - vol * D);
-        // stage the three input planes, zero-padded
+        // stage the three input planes, zero-padded, with asynchronous 16-byte copies (a zero
+        // source size fills the padding without reading global memory)
         for (int p = 0; p < 3; p++) {
             const int zz = z + p - 1;
             const bool pv = zz >= 0 && zz < D;
             for (int idx = tid; idx < NSL * 2; idx += blockDim.x) {
                 const int slot = idx >> 1, c = idx & 1;
                 const int y = slot / P, x = slot - (slot / P) * P;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (pv && slot < plane_slots && y >= 1 && y <= H && x >= 1 && x <= W) {
-                    const long long vox = ((vol * D + zz) * H + (y - 1)) * W + (x - 1);
-                    v = __ldg(reinterpret_cast<const uint4*>(X + vox * CH) + c);
-                }
-                *reinterpret_cast<uint4*>(sm + TC_A_OFF + ((p * 2 + c) * NSL + slot) * 16) = v;
+                const bool in = pv && slot < plane_slots && y >= 1 && y <= H && x >= 1 && x <= W;
+                const long long vox = in ? ((vol * D + zz) * H + (y - 1)) * W + (x - 1) : 0;
+                const void* src = reinterpret_cast<const uint4*>(X + vox * CH) + c;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(abase + uint32_t(((p * 2 + c) * NSL + slot) * 16)),
+                             "l"(src), "r"(in ? 16 : 0)
+                             : "memory");
             }
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
+            // descriptors differ only in their start address (bits 0-13, 16-byte units): the tap
+            // (dx, dy, dz) of tile t starts (dz + 1) 2 NSL + dy P + dx slots after the tile's slot
+            const uint64_t a0 = smem_desc(abase, uint32_t(NSL * 16), 128u);
+            const uint64_t b0 = smem_desc(wbase, uint32_t(CH * 16), 128u);
             for (int t = 0; t < ntile; t++) {
-                const int s0 = P + 1 + 128 * t;
-                for (int o = 0; o < TAPS; o++) {
-                    const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
-                    const uint32_t a = abase + uint32_t(((dz + 1) * 2 * NSL + s0 + dy * P + dx) * 16);
-                    const uint64_t ad = smem_desc(a, uint32_t(NSL * 16), 128u);
-                    const uint64_t bd = smem_desc(wbase + uint32_t(o * 2 * CH * 8 * 2), uint32_t(CH * 16), 128u);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + uint32_t(t * 16)),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(o));
-                }
+                const uint64_t at = a0 + uint64_t(P + 1 + 128 * t);
+                int o = 0;
+#pragma unroll
+                for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+                    for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                        for (int dx = -1; dx <= 1; dx++, o++) {
+                            const uint64_t ad = at + uint64_t(dz * 2 * NSL + dy * P + dx);
+                            const uint64_t bd = b0 + uint64_t(o * 2 * CH * 8 * 2 / 16);
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + uint32_t(t * 16)),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(o));
+                        }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
         }
