@@ -73,7 +73,13 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pre
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(pred ? 4 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Cells whose pulls are in flight per thread in the FP32 column walk (pipeline depth).
+#ifndef LBM_CP_STAGES
+#define LBM_CP_STAGES 2
+#endif
 
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
 // v holds f (or f - w rho0 when shifted) on entry and f-tilde on exit.  R is rho (or rho - rho0).
@@ -262,7 +268,8 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
 template <typename T, typename C>
 struct StepSmem {
     static constexpr bool kAsync = sizeof(T) == 4;
-    C slow[kAsync ? 2 : 1][19][256];
+    static constexpr int kStages = LBM_CP_STAGES;
+    C slow[kAsync ? kStages : 1][19][256];
 };
 
 // The work of CTA `bid` of one launch of F_L(s) (see step_kernel); every thread of the CTA calls it.
@@ -356,12 +363,13 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
             }
         };
         if constexpr (kAsync) {
-            // two-deep pipeline: the pulls of cell k+1 are in flight while cell k collides
+            // pipeline: the pulls of the next kStages - 1 cells are in flight while cell k collides
+            constexpr int kStages = StepSmem<T, C>::kStages;
             auto issue = [&](int k) -> uint32_t {
                 const int z = z0 + k;
                 const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
                 const bool live = !((solid >> z) & 1u);
-                C(&stage)[19][256] = slow[k & 1];
+                C(&stage)[19][256] = slow[k % kStages];
                 const T* p = src;
                 cp_async4(&stage[0][tid], p + cidx, live);
 #pragma unroll
@@ -372,16 +380,24 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
                 cp_async_commit();
                 return (need_mask && live) ? __ldg(a.lv.link + cidx) : 0u;
             };
-            uint32_t m_next = issue(0);
-            for (int k = 0; k < zc; k++) {
-                const uint32_t m = m_next;
-                if (k + 1 < zc) m_next = issue(k + 1);
+            uint32_t mq[kStages - 1];
+#pragma unroll
+            for (int j = 0; j < kStages - 1; j++) {
+                mq[j] = 0u;
+                if (j < zc) mq[j] = issue(j);
                 else cp_async_commit();
-                cp_async_wait1();
+            }
+            for (int k = 0; k < zc; k++) {
+                const uint32_t m = mq[0];
+#pragma unroll
+                for (int j = 0; j + 1 < kStages - 1; j++) mq[j] = mq[j + 1];
+                if (k + kStages - 1 < zc) mq[kStages - 2] = issue(k + kStages - 1);
+                else cp_async_commit();
+                cp_async_wait<kStages - 1>();
                 const int z = z0 + k;
                 if ((solid >> z) & 1u) continue;
                 const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
-                C(&stage)[19][256] = slow[k & 1];
+                C(&stage)[19][256] = slow[k % kStages];
                 C v[19];
 #pragma unroll
                 for (int q = 0; q < 19; q++) v[q] = stage[q][tid];
