@@ -153,27 +153,33 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TC_TM_OFF);
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
     const int H = d.H, W = d.W, D = d.D;
-    const int plane_slots = (H + 2) * P;
+    // the padding slots (plane borders and the tail beyond the plane) are zero for every unit:
+    // fill them once; each unit then copies only the interior rows
+    for (int i = tid; i < 6 * NSL; i += blockDim.x) *reinterpret_cast<uint4*>(sm + TC_A_OFF + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+    // this thread's place in the interior row copies: chunk xc of rows r0, r0 + rpp, ...
+    const int cpr = 2 * W, rpp = blockDim.x / cpr;
+    const int r0 = tid / cpr, xc = tid - (tid / cpr) * cpr;
+    const bool copier = r0 < rpp;
     uint32_t phase = 0;
     for (long long unit = blockIdx.x; unit < (long long)d.nvol * D; unit += gridDim.x) {
         const long long vol = unit / D;
         const int z = int(unit - vol * D);
-        // stage the three input planes, zero-padded, with asynchronous 16-byte copies (a zero
-        // source size fills the padding without reading global memory)
-        for (int p = 0; p < 3; p++) {
-            const int zz = z + p - 1;
-            const bool pv = zz >= 0 && zz < D;
-            for (int idx = tid; idx < NSL * 2; idx += blockDim.x) {
-                const int slot = idx >> 1, c = idx & 1;
-                const int y = slot / P, x = slot - (slot / P) * P;
-                const bool in = pv && slot < plane_slots && y >= 1 && y <= H && x >= 1 && x <= W;
-                const long long vox = in ? ((vol * D + zz) * H + (y - 1)) * W + (x - 1) : 0;
-                const void* src = reinterpret_cast<const uint4*>(X + vox * CH) + c;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(abase + uint32_t(((p * 2 + c) * NSL + slot) * 16)),
-                             "l"(src), "r"(in ? 16 : 0)
-                             : "memory");
+        // stage the interiors of the three input planes with asynchronous 16-byte copies; a plane
+        // outside the volume is zero (a zero source size writes zeros without reading)
+        if (copier)
+            for (int p = 0; p < 3; p++) {
+                const int zz = z + p - 1;
+                const bool pv = zz >= 0 && zz < D;
+                const long long row0 = (vol * D + (pv ? zz : 0)) * H;
+                for (int y = r0; y < H; y += rpp) {
+                    const int x = xc >> 1, c = xc & 1;
+                    const int slot = (y + 1) * P + x + 1;
+                    const void* src = reinterpret_cast<const uint4*>(X + ((row0 + y) * W + x) * CH) + c;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(abase + uint32_t(((p * 2 + c) * NSL + slot) * 16)),
+                                 "l"(src), "r"(pv ? 16 : 0)
+                                 : "memory");
+                }
             }
-        }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
