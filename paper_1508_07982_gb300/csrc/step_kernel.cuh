@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -645,22 +646,34 @@ __global__ void __launch_bounds__(256) reduce_level_kernel(const DevLevel lv, in
     const int64_t nown_cells = int64_t(lv.nown) << (3 * LB);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     const T* f = static_cast<const T*>(lv.f[cur]);
+    // With shifted storage a cell's 19 values are small deviations (f - w rho0), so the cell's sums
+    // are formed in FP32 (an error near 1e-10 per cell) and only the totals run in FP64: GB300's
+    // FP64 pipe would otherwise make this the slowest kernel of a step.  FP64 storage sums in FP64.
+    using A = typename std::conditional<Store<T>::shifted, float, double>::type;
+    const A ax = A(rho0 * P->acc[0]), ay = A(rho0 * P->acc[1]), az = A(rho0 * P->acc[2]);
+    int64_t cells = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nown_cells; i += int64_t(gridDim.x) * blockDim.x) {
         if (lv.cell[i] != CK_FLUID) continue;
-        double R = 0, jx = 0, jy = 0, jz = 0;
+        A R = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int q = 0; q < 19; q++) {
-            const double v = double(Store<T>::ld(f + q * lv.ncells + i));
+            const A v = A(Store<T>::ld(f + q * lv.ncells + i));
             R += v;
-            jx += dex(q) * v;
-            jy += dey(q) * v;
-            jz += dez(q) * v;
+            if (dex(q)) jx += dex(q) > 0 ? v : -v;
+            if (dey(q)) jy += dey(q) > 0 ? v : -v;
+            if (dez(q)) jz += dez(q) > 0 ? v : -v;
         }
-        s[0] += w * (Store<T>::shifted ? rho0 + R : R);
-        s[1] += w * (jx - rho0 * P->acc[0]);
-        s[2] += w * (jy - rho0 * P->acc[1]);
-        s[3] += w * (jz - rho0 * P->acc[2]);
+        s[0] += double(R);
+        s[1] += double(jx - ax);
+        s[2] += double(jy - ay);
+        s[3] += double(jz - az);
+        cells++;
     }
+    // volume weight, and rho0 per fluid cell for the shifted layouts
+    s[0] = w * (Store<T>::shifted ? s[0] + rho0 * double(cells) : s[0]);
+    s[1] *= w;
+    s[2] *= w;
+    s[3] *= w;
     __shared__ double red[4][8];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
