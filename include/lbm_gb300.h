@@ -179,11 +179,16 @@ lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double
 lbm_status lbm_get_pdfs(lbm_forest* f, int32_t level, double* pdfs, int32_t on_device);
 lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_t on_device);
 
-/* Volume-weighted totals over owned fluid cells of all levels, accumulated in FP64: out[0] =
- * sum 8^-L rho, out[1..3] = sum 8^-L j with j = sum_a e_a f_a of the post-streaming state.  With
- * FP32/FP16 storage each cell's 19-term sums are formed in FP32 from the shifted values (their
- * error is near 1e-10 per cell); FP64 storage sums in FP64 throughout.  out is host memory;
- * synchronises the stream.  Returns LBM_ENONFINITE if a total is not finite. */
+/* Volume-weighted totals over owned fluid cells of all levels: out[0] = sum 8^-L rho, out[1..3] =
+ * sum 8^-L j with j = sum_a e_a f_a of the post-streaming state (the moments the last collision
+ * of each cell started from).  After lbm_step_coarse the step kernels have recorded them: each
+ * level's last sub-step of the coarse step sums its cells' moments per warp in the compute type,
+ * and this call adds the warp sums in FP64 (no PDF is read).  After lbm_init_equilibrium,
+ * lbm_set_pdfs, a batched step or an autotune they are summed from the stored PDFs instead, with
+ * j = sum_a e_a f~_a - rho0 a (the collision adds rho0 a): FP32 per-cell sums of the shifted values
+ * with FP32/FP16 storage, FP64 with FP64 storage.  The two agree up to the rounding of the stored
+ * values.  out is host memory; synchronises the stream.  Returns LBM_ENONFINITE if a total is not
+ * finite. */
 lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
 
 /* ---- measurement -------------------------------------------------------------------------

@@ -52,6 +52,7 @@ struct Launch {
     int level, substep, grid;
     int type;   // 0: stream-collide F_L(substep), 1: explosion E_L
     int lzc;    // log2 cells per thread along z of this level's stream-collide launch
+    int tot = 0;   // 1: the level's last sub-step of a coarse step, which records the totals
 };
 
 struct DevBuf {
@@ -64,6 +65,7 @@ struct DevBuf {
     uint8_t* colspec = nullptr;
     uint32_t* gwork[2] = {nullptr, nullptr};
     uint32_t* ework = nullptr;
+    double* wpart = nullptr;   // per-warp moments of the level's last sub-step
 };
 
 __global__ void reduce_final_kernel(const double* partial, int n, double* out) {
@@ -165,6 +167,8 @@ struct lbm_forest {
     int64_t updates = 0;
     int lzc = 3;        // upper bound of log2 cells per thread along z (small levels use fewer)
     int minb = 3;       // CTAs per SM of the step-kernel variant
+    std::vector<int64_t> tot_warps;   // per level: warp entries its recording launch writes
+    bool totals_valid = false;        // the recorded moments describe the current state
     std::vector<double*> uprev;   // per level, the velocity of the previous residual call
     double* d_rpart = nullptr;    // residual partial sums
 };
@@ -205,6 +209,7 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.wall = f->d_wall;
     a.rho0 = f->plan.d.rho0;
     a.inv_rho0 = 1.0 / f->plan.d.rho0;
+    a.totals = l.tot ? f->buf[L].wpart : nullptr;
     return a;
 }
 
@@ -244,6 +249,19 @@ void build_schedule(lbm_forest* f) {
         push(L, 2);
     };
     rec(0);
+    // the last sub-step of each level in the coarse step records the totals of what it writes; the
+    // warp layout of what an earlier schedule recorded no longer matches
+    f->totals_valid = false;
+    f->tot_warps.assign(n, 0);
+    for (int L = 0; L < n; L++)
+        for (size_t k = f->sched.size(); k-- > 0;)
+            if (f->sched[k].level == L && f->sched[k].type == 0) {
+                Launch& l = f->sched[k];
+                l.tot = 1;
+                const int64_t units = int64_t(f->plan.lv[L].nown) * B * B * (B >> l.lzc);
+                f->tot_warps[L] = units / 32;   // the warps with work: entries 0 .. units/32 - 1
+                break;
+            }
 }
 
 // Enqueues every kernel of one coarse step on stream s; cur holds the two-grid parity of each
@@ -409,6 +427,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.gwork[0]);
         cudaFree(b.gwork[1]);
         cudaFree(b.ework);
+        cudaFree(b.wpart);
     }
     for (double* p : f->uprev) cudaFree(p);
     cudaFree(f->d_rpart);
@@ -464,6 +483,9 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
             (s = upload(&b.gwork[0], V.gwork[0])) || (s = upload(&b.gwork[1], V.gwork[1])) ||
             (s = upload(&b.ework, V.ework)))
             return bail(s);
+        // per-warp totals of the recording launch, sized for one cell per thread (the most warps)
+        if (cudaMalloc(&b.wpart, size_t((int64_t(V.nown) * B3 + 255) / 256 * 8 + 1) * 4 * sizeof(double)) != cudaSuccess)
+            return bail(fail(LBM_ENOMEM, "cannot allocate the totals of level %d", L));
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
         g.f[1] = b.f[1];
@@ -511,6 +533,14 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
         cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
         return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
+    // host staging of (rho, u) for the largest level, sized once: growing it later would free and
+    // allocate device memory (cudaFree synchronises) in the middle of a caller's loop
+    {
+        int64_t nmax = 0;
+        for (int L = 0; L < P.nlev; L++) nmax = std::max(nmax, owned_cells(f, L));
+        lbm_status st = ensure_stage(f, size_t(nmax) * 4 * sizeof(double));
+        if (st) return bail(st);
+    }
     // cells per thread along z: 4 for 32^3 blocks, 2 for 16^3, 1 for 8^3
     f->lzc = P.LB - 3;
     build_schedule(f);
@@ -593,6 +623,7 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
         }
         CU(cudaGetLastError());
         f->init_mask = (1u << P.nlev) - 1;
+        f->totals_valid = false;
         return LBM_OK;
     }
     lbm_status s = check_level(f, level);
@@ -613,6 +644,7 @@ lbm_status lbm_init_equilibrium(lbm_forest* f, int32_t level, const double* rho,
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
+    f->totals_valid = false;
     return LBM_OK;
 }
 
@@ -641,6 +673,7 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
         CU(cudaGraphLaunch(f->exec[p], f->stream));
         f->cur[0] ^= 1;
     }
+    if (n_steps > 0) f->totals_valid = true;
     return LBM_OK;
 }
 
@@ -703,6 +736,7 @@ lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_
     CU(cudaGetLastError());
     if (!on_device) CU(cudaStreamSynchronize(f->stream));
     f->init_mask |= 1u << level;
+    f->totals_valid = false;
     return LBM_OK;
 }
 
@@ -710,9 +744,15 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
     if (!f || !out) return fail(LBM_EINVAL, "NULL argument");
     const Plan& P = f->plan;
     int off = 0;
+    const bool shifted = P.d.precision != LBM_FP64;
     for (int L = 0; L < P.nlev; L++) {
-        f->L->reduce(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, std::ldexp(1.0, -3 * L),
-                     f->d_partial + 4 * off, f->red_grid[L], f->stream);
+        const double w = std::ldexp(1.0, -3 * L);
+        if (f->totals_valid)   // the step recorded the moments of this state: sum them
+            f->L->totals(f->buf[L].wpart, f->tot_warps[L], w, shifted ? P.d.rho0 * double(P.lv[L].nfluid) : 0.0,
+                         f->d_partial + 4 * off, f->red_grid[L], f->stream);
+        else
+            f->L->reduce(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, w, f->d_partial + 4 * off,
+                         f->red_grid[L], f->stream);
         off += f->red_grid[L];
     }
     reduce_final_kernel<<<1, 256, 0, f->stream>>>(f->d_partial, f->red_total, f->d_out);
@@ -904,6 +944,7 @@ lbm_status tune(const std::vector<lbm_forest*>& fs, cudaStream_t s, int LB, int 
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     lbm_status rs = restore_snapshot(fs, s, sn);
+    for (lbm_forest* f : fs) f->totals_valid = false;
     free_snapshot(sn);
     if (st) return st;
     if (rs) return rs;
@@ -1163,7 +1204,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int32_t n_steps) {
             if (s) return s;
         }
         CU(cudaGraphLaunch(b->exec[p], b->stream));
-        for (lbm_forest* f : b->fs) f->cur[0] ^= 1;
+        for (lbm_forest* f : b->fs) {
+            f->cur[0] ^= 1;
+            f->totals_valid = false;   // batched launches record no totals
+        }
     }
     return LBM_OK;
 }

@@ -51,6 +51,7 @@ struct StepArgs {
     const LevelParams* params;
     const double* wall;   // [6][19] 6 w_a rho0 (e_a . u_w) per face
     double rho0, inv_rho0;
+    double* totals;       // per-warp post-streaming moments of the owned cells, or NULL
 };
 
 // Bits of the per-cell link mask.
@@ -70,6 +71,7 @@ struct Launchers {
     void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
                    int grid, cudaStream_t s);
+    void (*totals)(const double* wpart, int64_t n, double w, double shift, double* partial, int grid, cudaStream_t s);
     void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s);
     // One phase of a batch of forests: args[n] per forest, prefix[n+1] its first virtual CTA;
     // `grid` persistent CTAs walk the `total` virtual CTAs.

@@ -52,6 +52,11 @@ struct LaunchImpl {
         if (grid <= 0) return;
         reduce_level_kernel<T><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, w, partial);
     }
+    static void totals(const double* wpart, int64_t n, double w, double shift, double* partial, int grid,
+                       cudaStream_t s) {
+        if (grid <= 0) return;
+        totals_level_kernel<T><<<grid, 256, 0, s>>>(wpart, n, w, shift, partial);
+    }
     static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s) {
         if (lv.nework <= 0) return;
         explode_kernel<T><<<(lv.nework + 255) / 256, 256, 0, s>>>(lv, co, cur, cur_c);
@@ -80,7 +85,8 @@ struct LaunchImpl {
         explode_batch_kernel<T><<<grid, 256, 0, s>>>(args, prefix, n, total);
     }
     static const Launchers& get() {
-        static const Launchers L{&step, &init, &macro, &get_pdfs, &set_pdfs, &reduce, &explode, &step_batch, &explode_batch};
+        static const Launchers L{&step,   &init,    &macro,      &get_pdfs,     &set_pdfs,
+                                 &reduce, &totals,  &explode,    &step_batch,   &explode_batch};
         return L;
     }
 };

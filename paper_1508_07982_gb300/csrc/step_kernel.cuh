@@ -88,8 +88,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // f^eq of Eq. (fequ) and F_a = 3 w_a rho0 e_a . a (Sec. 2.1); the velocity inside f^eq is
 // sum_a e_a f_a / rho0, unmodified by the force.
 // The body force enters as fa = 3 rho0 a (three values): F_q = w_q (e_q . fa), F_opp(q) = -F_q.
-template <typename C, int COLL>
-__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0) {
+// rec(R, jx, jy, jz) receives the post-streaming moments the collision starts from.
+template <typename C, int COLL, typename Rec>
+__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0, Rec&& rec) {
     C R = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
     for (int q = 0; q < 19; q++) {
@@ -98,6 +99,7 @@ __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3]
         if (dey(q)) jy += dey(q) > 0 ? v[q] : -v[q];
         if (dez(q)) jz += dez(q) > 0 ? v[q] : -v[q];
     }
+    rec(R, jx, jy, jz);
     const C ux = jx * inv_rho0, uy = jy * inv_rho0, uz = jz * inv_rho0;
     const C usq = ux * ux + uy * uy + uz * uz;
     const C base = C(1.5) * rho0 * usq;
@@ -271,6 +273,7 @@ struct StepSmem {
     static constexpr bool kAsync = sizeof(T) == 4;
     static constexpr int kStages = LBM_CP_STAGES;
     C slow[kAsync ? kStages : 1][19][256];
+    C tot[4][256];   // per-thread moments of the recording launch
 };
 
 // The work of CTA `bid` of one launch of F_L(s) (see step_kernel); every thread of the CTA calls it.
@@ -291,7 +294,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
 
     if (bid < owned_ctas) {
         const int64_t u = bid * 256 + tid;
-        if (u >= owned_units) return;
+        // totals of the state this launch writes (the level's last sub-step of a coarse step): the
+        // post-streaming moments of its owned fluid cells, one {R, jx, jy, jz} per warp, summed in
+        // shared memory per thread (registers held across the cell loop would spill)
+        const bool want_tot = a.totals != nullptr;
+        C(&tot)[4][256] = smem.tot;
+        if (want_tot)
+            for (int k = 0; k < 4; k++) tot[k][tid] = C(0);
+        if (u >= owned_units) return;   // whole warps: owned_units is a multiple of 64
         const int brick = int(u / upb);
         const int r = int(u - int64_t(brick) * upb);
         const int col = r & ((1 << B2s) - 1);
@@ -355,7 +365,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) v[q] = buf[q][tid];
             }
-            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0);
+            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0, [&](C R, C jx, C jy, C jz) {
+                if (want_tot) {
+                    tot[0][tid] += R;
+                    tot[1][tid] += jx;
+                    tot[2][tid] += jy;
+                    tot[3][tid] += jz;
+                }
+            });
             T* p = dst + cidx;
 #pragma unroll
             for (int q = 0; q < 19; q++) {
@@ -419,6 +436,17 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
                     v[q] = C(Store<T>::ld(p + src_index(q, z)));
                 }
                 finish(z, cidx, m, v, slow[0]);
+            }
+        }
+        if (want_tot) {
+            // the warp's sum in the compute type (FP64 arithmetic runs at a small fraction of the
+            // FP32 rate on this GPU, and a launch with one cell per thread would feel it)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                C t = tot[k][tid];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+                if ((tid & 31) == 0) a.totals[(bid * 8 + (tid >> 5)) * 4 + k] = double(t);
             }
         }
         return;
@@ -572,7 +600,7 @@ __global__ void init_kernel(const DevLevel lv, int cur, int LB, const LevelParam
         v[q] = C(dw(q) * (R + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
     }
     const C fa[3] = {C(P->fa[0]), C(P->fa[1]), C(P->fa[2])};
-    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0));
+    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0), [](C, C, C, C) {});
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         Store<T>::st(f + q * lv.ncells + i, v[q]);
@@ -640,6 +668,29 @@ __global__ void set_pdfs_kernel(const DevLevel lv, int cur, int LB, double rho0,
 
 // Per-CTA FP64 partial totals of one level: {w rho, w (j~ - rho0 a)} over owned fluid cells, with
 // w = 8^-L.  partial[blockIdx][4]; summed in a fixed order by reduce_final_kernel.
+
+
+// Volume-weighted totals of one level from the per-warp moments the step kernel left: n warp
+// entries {R, jx, jy, jz}; shift = rho0 x (fluid cells) for the shifted layouts (R sums f - w rho0),
+// force = rho0 a (the stored state is post-collision, the moments post-streaming: no correction).
+template <typename T>
+__global__ void __launch_bounds__(256) totals_level_kernel(const double* __restrict__ wpart, int64_t n, double w,
+                                                           double shift, double* partial) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        for (int k = 0; k < 4; k++) s[k] += wpart[4 * i + k];
+    __shared__ double red[4][256];
+    for (int k = 0; k < 4; k++) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (int(threadIdx.x) < h)
+            for (int k = 0; k < 4; k++) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4)
+        partial[blockIdx.x * 4 + threadIdx.x] = w * (red[threadIdx.x][0] + (threadIdx.x == 0 && blockIdx.x == 0 ? shift : 0.0));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_level_kernel(const DevLevel lv, int cur, int LB, const LevelParams* P,
                                                           double rho0, double w, double* partial) {

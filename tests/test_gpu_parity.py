@@ -263,6 +263,46 @@ def _mirror_gap(f, level, axis):
     return float(np.abs(u[:, ok] - um[:, j][:, ok]).max())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32s", "fp16s"])
+def test_recorded_totals_are_the_moments_of_the_streamed_state(lbm, precision):
+    """After a coarse step the totals are the moments the step's collisions started from, recorded
+    by the step kernel.  On a fully periodic single-level grid streaming permutes each direction's
+    values among the cells, so they equal the totals of the state before the step, summed here in
+    FP64 from its exact stored values.  The kernel sums each cell's 19 values, then the cells of a
+    warp (at most 32 per thread, then a 5-level shuffle tree), in the compute type (FP64, or FP32
+    from the shifted values f - w rho0), and the warps in FP64.  Recursive-summation bounds:
+    gamma_18 sum_q |f_q| per cell, gamma_40 of the same sums for the warp, gamma_64 (FP64) of the
+    cell totals for the rest."""
+    case = inputs.periodic_case(n=64, B=16, collision="trt", omega=1.7)
+    f = lbm.Forest(case, precision=precision)
+    f.init_fields(inputs.taylor_green_field(64))
+    f.step_coarse(2)
+    pd = f.get_pdfs(0)
+    e, w, _ = lbm.lbm_lattice()
+    rho0 = case["rho0"]
+    s = pd if precision == "fp64" else pd - w[:, None] * rho0       # exact: the stored values
+    f.step_coarse(1)
+    got = f.reduce_mass_momentum()
+    u = 2.0 ** -53 if precision == "fp64" else 2.0 ** -24
+    gamma = lambda k, u: k * u / (1 - k * u)
+
+    def check(got, pd, s):
+        ref = np.concatenate([[pd.sum()], (e.T.astype(float) @ pd).sum(axis=1)])
+        bound = (gamma(18, u) + gamma(40, u)) * np.abs(s).sum() + gamma(64, 2.0 ** -53) * np.abs(pd.sum(axis=0)).sum()
+        assert abs(got[0] - ref[0]) <= bound, (got[0] - ref[0], bound)
+        assert np.abs(got[1:] - ref[1:]).max() <= bound, (got[1:] - ref[1:], bound)
+        assert bound < 0.5          # a missing cell (rho near 1) would fail
+
+    check(got, pd, s)
+    # a new launch configuration drops the recorded moments: the totals are then summed from the
+    # stored state (no body force here, so j needs no correction)
+    lzc, minb = f.kernel_config()
+    f.set_kernel_config(lzc - 1, minb)
+    pd = f.get_pdfs(0)
+    check(f.reduce_mass_momentum(), pd, pd if precision == "fp64" else pd - w[:, None] * rho0)
+    f.close()
+
+
 def test_full_size_bench_workload_conserves_mass_and_symmetry(lbm):
     """Bench workload at full size (8.39M cells, 4 levels, 32^3 blocks) in FP64, in the launch
     configuration bench.py times: total mass is conserved to round-off and the flow stays
