@@ -388,12 +388,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
                 const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + x;
                 const bool live = !((solid >> z) & 1u);
                 C(&stage)[19][256] = slow[k % kStages];
-                const T* p = src;
-                cp_async4(&stage[0][tid], p + cidx, live);
+                if (live) {   // an obstacle cell's stage is never read: no copies
+                    const T* p = src;
+                    cp_async4(&stage[0][tid], p + cidx, true);
 #pragma unroll
-                for (int q = 1; q < 19; q++) {
-                    p += n;
-                    cp_async4(&stage[q][tid], p + src_index(q, z), live);
+                    for (int q = 1; q < 19; q++) {
+                        p += n;
+                        cp_async4(&stage[q][tid], p + src_index(q, z), true);
+                    }
                 }
                 cp_async_commit();
                 return (need_mask && live) ? __ldg(a.lv.link + cidx) : 0u;
