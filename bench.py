@@ -47,6 +47,7 @@ def _args():
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-forest leg")
     p.add_argument("--no-net", action="store_true", help="skip the warm-start net leg")
+    p.add_argument("--no-lid", action="store_true", help="skip the paper's lid-driven benchmark leg")
     return p.parse_args()
 
 
@@ -325,6 +326,49 @@ def _batch(lbm, torch, steps=500, warmup=5, serial_steps=50):
     return out
 
 
+# The paper's strong-scaling figure for its lid-driven benchmark (Sec. 5.2, SuperMUC table): 8.56M
+# cells, 32,768 cores, MPI + 4 OpenMP threads per process, FP64.  Context only: other machine,
+# other size.
+PAPER_LID_FINEST_STEPS_PER_S = 1113.97
+PAPER_LID_CELLS = 8.56e6
+
+
+def _lid(lbm, torch, peaks, peak_kind, steps=100, steps64=20):
+    """The paper's own benchmark cavity (Sec. 5.2): lid edges across the lid motion refined three
+    times, 3^3 roots of 32^3 cells (10.5M cells, 21 / 36 / 72 / 192 blocks on levels 0-3).  Per
+    precision: ms per coarse step, GLUPS, finest-level steps per second, the finest kernel's
+    roofline and each level's share of kernel time beside the table's workload shares."""
+    from paper_1508_07982_gb300 import inputs
+    case = inputs.lid_scaling_case()
+    out = {"workload": "lid-driven benchmark cavity of Sec. 5.2, 3^3 roots of 32^3 cells, lid edges across the "
+                       "lid motion refined 3x (4 levels, 21/36/72/192 blocks, %.2fM cells), rest start, TRT"
+                       % (sum(_fluid_counts_case(case)) / 1e6),
+           "paper_context": {"finest_steps_per_s": PAPER_LID_FINEST_STEPS_PER_S, "cells": PAPER_LID_CELLS,
+                             "machine": "SuperMUC, 32,768 cores, FP64 (strong scaling, Sec. 5.2)"},
+           "table_workload_share": [0.0110, 0.0376, 0.1502, 0.8013]}
+    for prec, k in (("fp32s", steps), ("fp16s", steps), ("fp64", steps64)):
+        f = lbm.Forest(case, precision=prec)
+        f.init_uniform()
+        f.step_coarse(3)
+        torch.cuda.synchronize()
+        ms = _timed_graph(f, torch, k)
+        _, lev = _timed_kernels(f, torch, k)
+        upd = f.cell_updates_per_coarse_step()
+        r = _roofline(f, lev, prec, peaks, peak_kind)
+        out[prec] = {"value": round(upd * k / (ms / 1e3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms / k, 5),
+                     "steps": k, "finest_steps_per_s": round(8 * k / (ms / 1e3), 1),
+                     "roofline": {kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "kernel")},
+                     "kernel_time_share": [lv["share"] for lv in r["per_level"]]}
+        f.close()
+    return out
+
+
+def _fluid_counts_case(case):
+    from paper_1508_07982_gb300 import lbm
+    p = lbm.Plan(case)
+    return [p.counts(L)["fluid"] for L in range(p.nlev)]
+
+
 def _net(lbm, torch, peaks, peak_kind, reps=10):
     """The warm-start net on 512 volumes of 18^3 voxels (8^3 blocks with a halo of 5): forward
     passes and training steps, each on the tcgen05 and the mma.sync tensor-core paths.  FLOPs count
@@ -467,6 +511,7 @@ def main():
     e2e = _e2e(lbm, torch, case, args.precision, min(args.steps, 200)) if rank == 0 and not args.no_e2e else None
     batch = _batch(lbm, torch) if rank == 0 and not args.no_batch else None
     net = _net(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_net else None
+    lid = _lid(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_lid else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(case)
@@ -482,6 +527,8 @@ def main():
         line["batch"] = batch
     if net:
         line["warm_start_net"] = net
+    if lid:
+        line["paper_lid_benchmark"] = lid
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()

@@ -58,6 +58,7 @@ def _cases():
     yield "cavity", inputs.cavity_case(), None
     yield "channel", inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True), None
     yield "poiseuille", inputs.plane_poiseuille_case(B=8, where="both"), None
+    yield "lid-scaling", inputs.lid_scaling_case(roots=(3, 1, 3), B=8), None
     yield "periodic-ball", inputs.periodic_case(n=64, B=8, collision="trt", omega=1.7,
                                                 regions=[("ball", 3, (5, 60, 33), 9.0)], lmax=3), None
     rng = np.random.default_rng(7)
@@ -75,7 +76,7 @@ def _cases():
                          regions=[]), refine
 
 
-@pytest.mark.parametrize("name", ["cavity", "channel", "poiseuille", "periodic-ball", "random"])
+@pytest.mark.parametrize("name", ["cavity", "channel", "poiseuille", "lid-scaling", "periodic-ball", "random"])
 def test_host_planner_matches_the_oracle_forest(lbm, oracle_mod, name):
     case, refine = next((c, r) for n, c, r in _cases() if n == name)
     memo = {}
@@ -99,3 +100,34 @@ def test_host_planner_matches_the_oracle_forest(lbm, oracle_mod, name):
         assert c["fluid"] == oc["fluid"]
         # the planner's ghost work list is the oracle's stream set minus its owned fluid cells
         assert c["ghost12"] == oc["stream"] - oc["fluid"]
+
+
+def _golden_lid_table():
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lid_driven_setup.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, *v = line.split()
+                rows[k] = [float(x) for x in v]
+    return rows
+
+
+@pytest.mark.parametrize("roots,B", [((3, 3, 3), 32), ((3, 1, 3), 8), ((3, 4, 3), 16)])
+def test_lid_scaling_forest_reproduces_the_benchmark_level_table(lbm, roots, B):
+    """The benchmark's level table (Sec. 5.2) from the planner's leaf counts: coverage = blocks
+    x 8^-L, workload = blocks x 2^L (cells per block are equal on every level, and level L takes
+    2^L steps per coarse step), memory = blocks, each as a share of its sum, within one unit of
+    the table's last digit (its memory row, 12/107 = 11.215 % printed as 11.22, sums to 100.00);
+    7 / 12 / 24 / 64 leaf blocks per 3 x 1 x 3 roots."""
+    p = lbm.Plan(inputs.lid_scaling_case(roots=roots, B=B))
+    assert p.nlev == 4
+    n = np.array([p.counts(L)["blocks"] for L in range(4)], dtype=float)
+    k = roots[1]
+    assert (n == np.array([7, 12, 24, 64]) * k).all()
+    cov = n * 8.0 ** -np.arange(4)
+    work = n * 2.0 ** np.arange(4)
+    got = {"coverage": 100 * cov / cov.sum(), "workload": 100 * work / work.sum(), "memory": 100 * n / n.sum()}
+    for key, ref in _golden_lid_table().items():
+        assert np.abs(got[key] - np.array(ref)).max() <= 0.01 + 1e-9, (key, got[key], ref)
+    # every leaf holds B^3 fluid cells (no obstacles)
+    assert sum(p.counts(L)["fluid"] for L in range(4)) == int(n.sum()) * B ** 3
