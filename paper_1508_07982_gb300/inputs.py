@@ -72,6 +72,64 @@ def lid_scaling_case(roots=(3, 3, 3), B=32, lid=0.05, lambda_e0=1.6, eps=1.0 / 3
                 lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0))
 
 
+def _square_meets_circle(y0, y1, z0, z1, R):
+    """The square [y0, y1] x [z0, z1] (coordinates from the circle's centre) meets the circle of
+    radius R: its nearest point lies inside and its farthest outside (or on it)."""
+    ny = 0.0 if y0 <= 0.0 <= y1 else min(abs(y0), abs(y1))
+    nz = 0.0 if z0 <= 0.0 <= z1 else min(abs(z0), abs(z1))
+    fy, fz = max(abs(y0), abs(y1)), max(abs(z0), abs(z1))
+    return ny * ny + nz * nz <= R * R <= fy * fy + fz * fz
+
+
+def pipe_poiseuille_case(D=60, B=8, lmax=0, where="wall", lambda_e0=0.6, accel=1e-6, paper_block=10):
+    """Pipe Poiseuille flow (Sec. 5.1): a pipe of diameter D level-0 cells along x, periodic in x
+    over one root block, driven by a body force; cells whose centre lies outside the pipe are
+    no-slip obstacles (staircase).  TRT with the magic parameter 3/16.
+
+    The cross-section is the smallest multiple of B that holds the pipe, with the pipe axis at
+    its centre.  Refinement to lmax:
+      "global"      every block;
+      "wall"        the blocks the pipe wall passes through (this forest's own blocks);
+      "wall-cover"  every block that overlaps (with positive area) a block the wall passes
+                    through in the paper's forest, whose blocks have paper_block level-0 cells
+                    per edge on a grid spanning the pipe (D = 60: 6 x 6 roots of 10^3 cells).
+    With B = 8 the first refines a thinner band around the wall than the paper's 10^3 blocks do,
+    the second a band that covers the paper's.  Returns (case, refine, flag, (centre, radius));
+    refine and flag are the callbacks of lbm_create_forest."""
+    n = -(-D // B)
+    c = n * B / 2.0
+    R = D / 2.0
+    case = dict(root=(1, n, n), B=B, lmax=lmax, collision="trt", rho0=1.0,
+                bc=["periodic"] * 2 + ["noslip"] * 4, bc_u=[(0.0, 0.0, 0.0)] * 6, spheres=[], regions=[],
+                lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(accel, 0.0, 0.0))
+
+    def refine(L, bx, by, bz, user):
+        if L >= lmax:
+            return 0
+        if where == "global":
+            return 1
+        s = B / 2.0 ** L
+        y0, y1, z0, z1 = by * s - c, (by + 1) * s - c, bz * s - c, (bz + 1) * s - c
+        if where == "wall":
+            return int(_square_meets_circle(y0, y1, z0, z1, R))
+        P = paper_block / 2.0 ** L
+        m = int(round(D / P))
+        for j in range(m):          # the paper-grid blocks of level L that this block overlaps
+            py0 = -R + j * P
+            if min(y1, py0 + P) <= max(y0, py0):
+                continue
+            for k in range(m):
+                pz0 = -R + k * P
+                if min(z1, pz0 + P) > max(z0, pz0) and _square_meets_circle(py0, py0 + P, pz0, pz0 + P, R):
+                    return 1
+        return 0
+
+    def flag(L, x, y, z, user):
+        return int((y - c) ** 2 + (z - c) ** 2 >= R * R)
+
+    return case, refine, flag, (c, R)
+
+
 def batch_cases(n=256, seed=SEED, B=16):
     """Small lid-driven cavities for stepping many forests together (the batched workload).
 
