@@ -71,7 +71,12 @@ typedef enum { LBM_FP64 = 0, LBM_FP32S = 1, LBM_FP16S = 2 } lbm_precision;
  *   regions       refinement regions: {kind, target level, p0..p5} with kind 0 = box
  *                 (lo xyz, hi xyz) and kind 1 = ball (centre xyz, radius); a block of level
  *                 L < target that overlaps the region (with positive volume, or closer than
- *                 the radius) is split. */
+ *                 the radius) is split.
+ *   u_shift       FP32S / FP16S storage: the stored value of direction a is f_a - f_a^eq(rho0,
+ *                 u_shift) (the precision extension's shift by w_a rho0, generalised to a
+ *                 reference velocity; zero gives f_a - w_a rho0).  Set it to the prevailing flow
+ *                 velocity (a channel's inlet plug): the stored deviations, and so the storage
+ *                 rounding, shrink with |u - u_shift|.  |u_shift| < 0.3; ignored for FP64. */
 typedef struct {
     int32_t root_blocks[3];
     int32_t block_cells;
@@ -85,6 +90,7 @@ typedef struct {
     double spheres[LBM_MAX_SPHERES][4];
     int32_t n_regions;
     double regions[LBM_MAX_REGIONS][8];
+    double u_shift[3];
 } lbm_forest_desc;
 
 /* Application callbacks (Sec. 3.3).  refine: return nonzero to split block (bx, by, bz) of
@@ -175,7 +181,9 @@ lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double
 
 /* PDFs of one level's owned cells, pdfs[19][n_cells] FP64 (unshifted f_a), block-major.  The
  * stored state is the post-collision state of the next step (the kernels store f-tilde).
- * lbm_set_pdfs writes the same layout back (checkpoint / resume, bit-exact for FP64). */
+ * lbm_set_pdfs writes the same layout back (checkpoint / resume, bit-exact for FP64 and FP16S;
+ * with FP32S and u_shift != 0 the FP64 f = v + f^eq(rho0, u_shift) of a stored value v below
+ * about 2e-9 can round, so a resumed run may differ in the last FP32 bits). */
 lbm_status lbm_get_pdfs(lbm_forest* f, int32_t level, double* pdfs, int32_t on_device);
 lbm_status lbm_set_pdfs(lbm_forest* f, int32_t level, const double* pdfs, int32_t on_device);
 

@@ -139,6 +139,7 @@ void lbm::set_last_error(const char* msg) { g_err = msg; }
 
 struct lbm_forest {
     Plan plan;
+    double u0[3] = {0.0, 0.0, 0.0};   // storage shift velocity (shifted layouts only)
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     const Launchers* L = nullptr;
@@ -210,6 +211,8 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.rho0 = f->plan.d.rho0;
     a.inv_rho0 = 1.0 / f->plan.d.rho0;
     a.totals = l.tot ? f->buf[L].wpart : nullptr;
+    for (int k = 0; k < 3; k++) a.two_u0[k] = float(2.0 * f->u0[k]);
+    for (int q = 0; q < Q; q++) a.e_two_u0[q] = float(2.0 * (EX[q] * f->u0[0] + EY[q] * f->u0[1] + EZ[q] * f->u0[2]));
     return a;
 }
 
@@ -458,6 +461,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     f->esize = elem_size(f->plan.d.precision);
     const Plan& P = f->plan;
     const int B3 = P.B * P.B * P.B;
+    for (int a = 0; a < 3; a++) f->u0[a] = P.d.precision == LBM_FP64 ? 0.0 : P.d.u_shift[a];
     auto bail = [&](lbm_status s) {
         std::string keep = g_err;
         lbm_destroy(f);
@@ -508,16 +512,22 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.nbricks = V.nbricks();
         g.ncells = ncells;
         for (int a = 0; a < 3; a++) g.N[a] = V.N[a];
+        for (int a = 0; a < 3; a++) g.u0[a] = f->u0[a];
         f->updates += V.nfluid << L;
     }
-    // wall terms 6 w_a rho0 (e_a . u_w) of velocity faces (velocity bounce-back)
-    std::vector<double> wall(6 * Q, 0.0);
-    for (int face = 0; face < 6; face++)
-        if (P.d.bc[face] == LBM_BC_VELOCITY)
-            for (int q = 0; q < Q; q++)
-                wall[face * Q + q] = 6.0 * weight(q) * P.d.rho0 *
-                                     (EX[q] * P.d.bc_velocity[face][0] + EY[q] * P.d.bc_velocity[face][1] +
-                                      EZ[q] * P.d.bc_velocity[face][2]);
+    // bounce-back terms 6 w_a rho0 (e_a . u_w) (velocity bounce-back; zero on no-slip faces and
+    // obstacles, row 7); with a storage shift by f^eq(rho0, u0) a bounce-back also moves the
+    // shift's odd part to the opposite direction, which adds -6 w_a rho0 (e_a . u0) to every row
+    std::vector<double> wall(8 * Q, 0.0);
+    for (int face = 0; face < 8; face++) {
+        if (face == 6 || (face < 6 && P.d.bc[face] == LBM_BC_PERIODIC)) continue;
+        double uw[3] = {0.0, 0.0, 0.0};
+        if (face < 6 && P.d.bc[face] == LBM_BC_VELOCITY)
+            for (int a = 0; a < 3; a++) uw[a] = P.d.bc_velocity[face][a];
+        for (int a = 0; a < 3; a++) uw[a] -= f->u0[a];
+        for (int q = 0; q < Q; q++)
+            wall[face * Q + q] = 6.0 * weight(q) * P.d.rho0 * (EX[q] * uw[0] + EY[q] * uw[1] + EZ[q] * uw[2]);
+    }
     lbm_status s;
     if ((s = upload(&f->d_wall, wall))) return bail(s);
     f->hp.assign(P.nlev, LevelParams{});
@@ -747,9 +757,13 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
     const bool shifted = P.d.precision != LBM_FP64;
     for (int L = 0; L < P.nlev; L++) {
         const double w = std::ldexp(1.0, -3 * L);
+        // the shifted layouts' per-cell offsets: sum_a f^eq_a(rho0, u0) = rho0 and sum_a e_a
+        // f^eq_a(rho0, u0) = rho0 u0
+        const double nf = shifted ? P.d.rho0 * double(P.lv[L].nfluid) : 0.0;
+        const double shift[4] = {nf, nf * f->u0[0], nf * f->u0[1], nf * f->u0[2]};
         if (f->totals_valid)   // the step recorded the moments of this state: sum them
-            f->L->totals(f->buf[L].wpart, f->tot_warps[L], w, shifted ? P.d.rho0 * double(P.lv[L].nfluid) : 0.0,
-                         f->d_partial + 4 * off, f->red_grid[L], f->stream);
+            f->L->totals(f->buf[L].wpart, f->tot_warps[L], w, shift, f->d_partial + 4 * off, f->red_grid[L],
+                         f->stream);
         else
             f->L->reduce(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, w, f->d_partial + 4 * off,
                          f->red_grid[L], f->stream);

@@ -584,6 +584,10 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
         err = "rho0 must be positive";
         return false;
     }
+    if (!(d->u_shift[0] * d->u_shift[0] + d->u_shift[1] * d->u_shift[1] + d->u_shift[2] * d->u_shift[2] < 0.09)) {
+        err = "u_shift must be finite with |u_shift| < 0.3";
+        return false;
+    }
     for (int a = 0; a < 3; a++) {
         if (d->root_blocks[a] < 1 || d->root_blocks[a] > 4096) {
             err = "root_blocks out of range";

@@ -37,6 +37,7 @@ struct DevLevel {
     int nown, nbricks;
     int64_t ncells;
     int N[3];
+    double u0[3];         // storage shift velocity: shifted layouts hold f - f^eq(rho0, u0); 0 for FP64
 };
 
 struct StepArgs {
@@ -49,9 +50,12 @@ struct StepArgs {
     int minb;             // CTAs per SM the kernel variant is compiled for (2, 3 or 4)
     int per;              // bit a set: axis a periodic
     const LevelParams* params;
-    const double* wall;   // [6][19] 6 w_a rho0 (e_a . u_w) per face
+    const double* wall;   // [8][19] bounce-back terms 6 w_a rho0 (e_a . (u_w - u0)): faces 0-5,
+                          // row 7 obstacles (u_w = 0), row 6 unused
     double rho0, inv_rho0;
     double* totals;       // per-warp post-streaming moments of the owned cells, or NULL
+    float two_u0[3];      // 2 u0 and 2 e_a . u0 of the storage shift (FP32 arithmetic; 0 unshifted)
+    float e_two_u0[19];
 };
 
 // Bits of the per-cell link mask.
@@ -71,7 +75,8 @@ struct Launchers {
     void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,
                    int grid, cudaStream_t s);
-    void (*totals)(const double* wpart, int64_t n, double w, double shift, double* partial, int grid, cudaStream_t s);
+    void (*totals)(const double* wpart, int64_t n, double w, const double shift[4], double* partial, int grid,
+                   cudaStream_t s);
     void (*explode)(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s);
     // One phase of a batch of forests: args[n] per forest, prefix[n+1] its first virtual CTA;
     // `grid` persistent CTAs walk the `total` virtual CTAs.

@@ -52,10 +52,10 @@ struct LaunchImpl {
         if (grid <= 0) return;
         reduce_level_kernel<T><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, w, partial);
     }
-    static void totals(const double* wpart, int64_t n, double w, double shift, double* partial, int grid,
+    static void totals(const double* wpart, int64_t n, double w, const double shift[4], double* partial, int grid,
                        cudaStream_t s) {
         if (grid <= 0) return;
-        totals_level_kernel<T><<<grid, 256, 0, s>>>(wpart, n, w, shift, partial);
+        totals_level_kernel<T><<<grid, 256, 0, s>>>(wpart, n, w, shift[0], shift[1], shift[2], shift[3], partial);
     }
     static void explode(const DevLevel& lv, const DevLevel& co, int cur, int cur_c, cudaStream_t s) {
         if (lv.nework <= 0) return;

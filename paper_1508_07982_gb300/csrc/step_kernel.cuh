@@ -7,7 +7,8 @@
 // later pull reads: the exploded layer-1 values that owned cells pull in sub-step 1 (Eq. ctof:
 // every ghost cell takes its coarse parent's post-collision PDFs) and the streamed values of
 // layers 1-2.  The ghost stream reads the other exploded values it needs from the coarse parent
-// in the coarser level's grid.  FP32/FP16 storage holds f - w rho0 ("shifted"); FP64 holds f.
+// in the coarser level's grid.  FP32/FP16 storage holds f - f^eq(rho0, u0) ("shifted"; u0 = 0
+// gives f - w rho0); FP64 holds f.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -66,6 +67,13 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
     return s;
 }
 
+// f^eq_q(rho0, u0): what the shifted layouts subtract from f_q (w_q rho0 when u0 = 0).
+__device__ __forceinline__ double shift_value(int q, double rho0, const double (&u0)[3]) {
+    const double eu = dex(q) * u0[0] + dey(q) * u0[1] + dez(q) * u0[2];
+    const double usq = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+    return dw(q) * rho0 * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+}
+
 // ------------------------------------------------------------------ shared-memory staging
 // 4-byte asynchronous copies global -> shared (LDGSTS); a false predicate zero-fills without
 // reading global memory.
@@ -83,14 +91,20 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 #endif
 
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
-// v holds f (or f - w rho0 when shifted) on entry and f-tilde on exit.  R is rho (or rho - rho0).
+// v holds f (or its shifted form) on entry and f-tilde on exit.  R is rho (or rho - rho0).
 // SRT: f~ = f - omega (f - f^eq) + F;  TRT: f~ = f - le (f+ - f^eq+) - lo (f- - f^eq-) + F, with
 // f^eq of Eq. (fequ) and F_a = 3 w_a rho0 e_a . a (Sec. 2.1); the velocity inside f^eq is
 // sum_a e_a f_a / rho0, unmodified by the force.
 // The body force enters as fa = 3 rho0 a (three values): F_q = w_q (e_q . fa), F_opp(q) = -F_q.
 // rec(R, jx, jy, jz) receives the post-streaming moments the collision starts from.
+// With FP32 arithmetic (the shifted layouts) v holds f - f^eq(rho0, u0): then R = rho - rho0,
+// j = rho0 (u - u0), and the equilibrium is taken relative to the same shift; two_u0 = 2 u0 and
+// e_two_u0[a] = 2 e_a . u0 (constants of the launch).  u0 = 0 gives the f - w rho0 layout.  FP64
+// arithmetic (unshifted storage) ignores them.
 template <typename C, int COLL, typename Rec>
-__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0, Rec&& rec) {
+__device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0,
+                                        const float (&two_u0)[3], const float (&e_two_u0)[19], Rec&& rec) {
+    constexpr bool kShift = sizeof(C) == 4;
     C R = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
     for (int q = 0; q < 19; q++) {
@@ -100,8 +114,11 @@ __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3]
         if (dez(q)) jz += dez(q) > 0 ? v[q] : -v[q];
     }
     rec(R, jx, jy, jz);
+    // d = j / rho0 (u - u0 when shifted): the shifted equilibrium's quadratic terms are
+    // (e.u)^2 - (e.u0)^2 = (e.d)(e.d + 2 e.u0) and u^2 - u0^2 = d.(d + 2 u0)
     const C ux = jx * inv_rho0, uy = jy * inv_rho0, uz = jz * inv_rho0;
-    const C usq = ux * ux + uy * uy + uz * uz;
+    C usq = ux * ux + uy * uy + uz * uz;
+    if constexpr (kShift) usq += ux * C(two_u0[0]) + uy * C(two_u0[1]) + uz * C(two_u0[2]);
     const C base = C(1.5) * rho0 * usq;
     {
         const C feq0 = C(dw(0)) * (R - base);
@@ -120,7 +137,9 @@ __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3]
         if (dez(q)) ea += dez(q) > 0 ? fa[2] : -fa[2];
         const C w = C(dw(q));
         const C Fq = w * ea;
-        const C eqp = w * (R + rho0 * (C(4.5) * eu * eu) - base);
+        C es = eu;
+        if constexpr (kShift) es += C(e_two_u0[q]);
+        const C eqp = w * (R + rho0 * (C(4.5) * eu * es) - base);
         const C eqm = w * rho0 * C(3.0) * eu;
         if (COLL == LBM_TRT) {
             const C fp = C(0.5) * (v[q] + v[p]);
@@ -208,7 +227,8 @@ template <> struct Par<float> {
 // links the link mask routes here:
 //   - coalescence (owned cells only): mean of the 8 finer children of x (Eq. ftoc);
 //   - obstacle or domain wall: bounce-back of the cell's own opposite value (Sec. 2.2), plus
-//     6 w rho0 e.u_w on velocity walls; a source beyond several faces takes the first of
+//     6 w rho0 e.(u_w - u0) (u_w = 0 except on velocity walls, u0 the storage shift); a source
+//     beyond several faces takes the first of
 //     z+, z-, y+, y-, x+, x-.  A ghost cell's own value in sub-step 1 is the exploded one;
 //   - otherwise the value of the source cell: stored (owned, or ghost layers 1-2 after their
 //     sub-step-1 stream), or exploded (ghost layers in sub-step 1, layer 3 always).
@@ -238,7 +258,9 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     if (nb >= 0) {
         const int64_t sidx = (int64_t(nb) << B3s) + ((sz & M) << (2 * LB)) + ((sy & M) << LB) + (sx & M);
         const uint8_t ck = __ldg(a.lv.cell + sidx);
-        if (ck == CK_SOLID) return own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
+        if (ck == CK_SOLID)
+            return (own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx)) +
+                   C(__ldg(a.wall + 7 * 19 + q));
         if (ck == CK_FAR) return qnan<C>();   // never a source: layer 4+ holds no value
         if (nb >= a.lv.nown && (a.substep == 1 || ck == CK_G3)) return acc.coarse(nb, sx & M, sy & M, sz & M, q);
         return acc.load(src, n, q, sidx);
@@ -343,16 +365,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
         auto finish = [&](int z, int cidx, uint32_t m, C (&v)[19], C (&buf)[19][256]) {
             const uint32_t mq = m & LINK_ALL;
             if (m & LINK_BOUNCE_ONLY) {
-                // every marked link bounces back: the cell's own opposite value, plus the wall
-                // term of one wall face (face 7: obstacle links only, no term)
+                // every marked link bounces back: the cell's own opposite value, plus the term of
+                // one wall face (face 7: obstacle links only)
                 const T* p = src + cidx;
                 const int face = int((m >> 25) & 7u);
 #pragma unroll
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) {
-                        C t = C(Store<T>::ld(p + int64_t(dopp(q)) * n));
-                        if (face != 7) t += C(__ldg(a.wall + face * 19 + q));
-                        v[q] = t;
+                        v[q] = C(Store<T>::ld(p + int64_t(dopp(q)) * n)) + C(__ldg(a.wall + face * 19 + q));
                     }
             } else if (m & LINK_COAL_ONLY) {
 #pragma unroll
@@ -365,7 +385,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) v[q] = buf[q][tid];
             }
-            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0, [&](C R, C jx, C jy, C jz) {
+            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0, a.two_u0, a.e_two_u0, [&](C R, C jx, C jy, C jz) {
                 if (want_tot) {
                     tot[0][tid] += R;
                     tot[1][tid] += jx;
@@ -598,11 +618,15 @@ __global__ void init_kernel(const DevLevel lv, int cur, int LB, const LevelParam
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         const double eu = dex(q) * vx + dey(q) * vy + dez(q) * vz;
-        const double R = Store<T>::shifted ? r - rho0 : r;
-        v[q] = C(dw(q) * (R + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
+        const double feq = dw(q) * (r + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+        v[q] = C(Store<T>::shifted ? feq - shift_value(q, rho0, lv.u0) : feq);
     }
     const C fa[3] = {C(P->fa[0]), C(P->fa[1]), C(P->fa[2])};
-    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0), [](C, C, C, C) {});
+    float two_u0[3], e_two_u0[19];
+    for (int k = 0; k < 3; k++) two_u0[k] = float(2.0 * lv.u0[k]);
+#pragma unroll
+    for (int q = 0; q < 19; q++) e_two_u0[q] = float(2.0 * (dex(q) * lv.u0[0] + dey(q) * lv.u0[1] + dez(q) * lv.u0[2]));
+    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0), two_u0, e_two_u0, [](C, C, C, C) {});
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         Store<T>::st(f + q * lv.ncells + i, v[q]);
@@ -634,10 +658,10 @@ __global__ void macro_kernel(const DevLevel lv, int cur, int LB, const LevelPara
         jz += dez(q) * v;
     }
     if (rho) rho[i] = Store<T>::shifted ? rho0 + R : R;
-    if (u) {
-        u[i] = jx / rho0 - 0.5 * P->acc[0];
-        u[nown_cells + i] = jy / rho0 - 0.5 * P->acc[1];
-        u[2 * nown_cells + i] = jz / rho0 - 0.5 * P->acc[2];
+    if (u) {   // the shifted layouts hold j - rho0 u0
+        u[i] = jx / rho0 + lv.u0[0] - 0.5 * P->acc[0];
+        u[nown_cells + i] = jy / rho0 + lv.u0[1] - 0.5 * P->acc[1];
+        u[2 * nown_cells + i] = jz / rho0 + lv.u0[2] - 0.5 * P->acc[2];
     }
 }
 
@@ -650,7 +674,7 @@ __global__ void get_pdfs_kernel(const DevLevel lv, int cur, int LB, double rho0,
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         const double v = double(Store<T>::ld(f + q * lv.ncells + i));
-        out[q * nown_cells + i] = Store<T>::shifted ? v + dw(q) * rho0 : v;
+        out[q * nown_cells + i] = Store<T>::shifted ? v + shift_value(q, rho0, lv.u0) : v;
     }
 }
 
@@ -663,7 +687,8 @@ __global__ void set_pdfs_kernel(const DevLevel lv, int cur, int LB, double rho0,
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         double v = __longlong_as_double(0x7ff8000000000000ULL);
-        if (i < nown_cells && lv.cell[i] == CK_FLUID) v = Store<T>::shifted ? in[q * nown_cells + i] - dw(q) * rho0 : in[q * nown_cells + i];
+        if (i < nown_cells && lv.cell[i] == CK_FLUID)
+            v = Store<T>::shifted ? in[q * nown_cells + i] - shift_value(q, rho0, lv.u0) : in[q * nown_cells + i];
         Store<T>::st_d(f + q * lv.ncells + i, v);
     }
 }
@@ -673,11 +698,12 @@ __global__ void set_pdfs_kernel(const DevLevel lv, int cur, int LB, double rho0,
 
 
 // Volume-weighted totals of one level from the per-warp moments the step kernel left: n warp
-// entries {R, jx, jy, jz}; shift = rho0 x (fluid cells) for the shifted layouts (R sums f - w rho0),
-// force = rho0 a (the stored state is post-collision, the moments post-streaming: no correction).
+// entries {R, jx, jy, jz}, plus {s0, s1, s2, s3} = (fluid cells) x {rho0, rho0 u0} for the shifted
+// layouts (they sum f - f^eq(rho0, u0)).  The moments are post-streaming: no force correction.
 template <typename T>
 __global__ void __launch_bounds__(256) totals_level_kernel(const double* __restrict__ wpart, int64_t n, double w,
-                                                           double shift, double* partial) {
+                                                           double s0, double s1, double s2, double s3,
+                                                           double* partial) {
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         for (int k = 0; k < 4; k++) s[k] += wpart[4 * i + k];
@@ -689,8 +715,10 @@ __global__ void __launch_bounds__(256) totals_level_kernel(const double* __restr
             for (int k = 0; k < 4; k++) red[k][threadIdx.x] += red[k][threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x < 4)
-        partial[blockIdx.x * 4 + threadIdx.x] = w * (red[threadIdx.x][0] + (threadIdx.x == 0 && blockIdx.x == 0 ? shift : 0.0));
+    if (threadIdx.x < 4) {
+        const double sh = threadIdx.x == 0 ? s0 : threadIdx.x == 1 ? s1 : threadIdx.x == 2 ? s2 : s3;
+        partial[blockIdx.x * 4 + threadIdx.x] = w * (red[threadIdx.x][0] + (blockIdx.x == 0 ? sh : 0.0));
+    }
 }
 
 template <typename T>
@@ -699,7 +727,7 @@ __global__ void __launch_bounds__(256) reduce_level_kernel(const DevLevel lv, in
     const int64_t nown_cells = int64_t(lv.nown) << (3 * LB);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     const T* f = static_cast<const T*>(lv.f[cur]);
-    // With shifted storage a cell's 19 values are small deviations (f - w rho0), so the cell's sums
+    // With shifted storage a cell's 19 values are small deviations (f - f^eq(rho0, u0)), so the cell's sums
     // are formed in FP32 (an error near 1e-10 per cell) and only the totals run in FP64: GB300's
     // FP64 pipe would otherwise make this the slowest kernel of a step.  FP64 storage sums in FP64.
     using A = typename std::conditional<Store<T>::shifted, float, double>::type;
@@ -722,11 +750,12 @@ __global__ void __launch_bounds__(256) reduce_level_kernel(const DevLevel lv, in
         s[3] += double(jz - az);
         cells++;
     }
-    // volume weight, and rho0 per fluid cell for the shifted layouts
-    s[0] = w * (Store<T>::shifted ? s[0] + rho0 * double(cells) : s[0]);
-    s[1] *= w;
-    s[2] *= w;
-    s[3] *= w;
+    // volume weight, and rho0 (mass) and rho0 u0 (momentum) per fluid cell for the shifted layouts
+    const double nc = Store<T>::shifted ? rho0 * double(cells) : 0.0;
+    s[0] = w * (s[0] + nc);
+    s[1] = w * (s[1] + nc * lv.u0[0]);
+    s[2] = w * (s[2] + nc * lv.u0[1]);
+    s[3] = w * (s[3] + nc * lv.u0[2]);
     __shared__ double red[4][8];
 #pragma unroll
     for (int k = 0; k < 4; k++) {

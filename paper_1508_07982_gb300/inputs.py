@@ -20,6 +20,7 @@ Case dict keys:
             a block below `level` that overlaps the region is split (Sec. 3.3)
   lambda_e0, magic, accel   coarse relaxation rate, TRT magic parameter, body
             acceleration on level 0 (Sec. 2.3 scales them per level)
+  u_shift   optional: FP32S/FP16S storage holds f - f^eq(rho0, u_shift) (default 0)
 All coordinates are in level-0 cell units; cell (i, j, k) of level L has its
 centre at ((i + .5) / 2^L, ...).
 """
@@ -216,9 +217,10 @@ def periodic_case(n=64, B=16, collision="srt", omega=1.9, regions=(), lmax=0):
 SPHERE_CHANNEL_RADII = (34.0, 12.0, 6.0)
 
 
-def sphere_channel_case(H=64, B=32, radii=SPHERE_CHANNEL_RADII, u_in=0.04, Re=100.0, inlet_outlet=False):
+def sphere_channel_case(H=64, B=32, radii=SPHERE_CHANNEL_RADII, u_in=0.04, Re=100.0, inlet_outlet=False,
+                        shift=True):
     """Channel 4H x H x H past a sphere of radius 0.1 H at (H, H/2, H/2), started from the plug
-    flow (u_in, 0, 0).
+    flow (u_in, 0, 0).  With shift, FP32S/FP16S storage holds f - f^eq(rho0, plug) (u_shift).
 
     Four levels: blocks within radii[L-1] (level-0 cells, scaled with H/64) of the sphere centre
     are refined towards level L.  The relaxation rate follows from Re on the sphere diameter.
@@ -237,7 +239,8 @@ def sphere_channel_case(H=64, B=32, radii=SPHERE_CHANNEL_RADII, u_in=0.04, Re=10
     return dict(root=(4 * H // B, H // B, H // B), B=B, lmax=len(radii), collision="trt",
                 rho0=1.0, bc=bc, bc_u=[(u_in, 0.0, 0.0)] * 2 + [(0.0, 0.0, 0.0)] * 4,
                 spheres=[(c[0], c[1], c[2], 0.1 * H)], regions=regions,
-                lambda_e0=le0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0), u_init=(u_in, 0.0, 0.0))
+                lambda_e0=le0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0), u_init=(u_in, 0.0, 0.0),
+                u_shift=(u_in if shift else 0.0, 0.0, 0.0))
 
 
 def plane_poiseuille_case(B=4, ny_roots=4, nxz_roots=1, where="bottom", lambda_e0=0.5, accel=1e-5):

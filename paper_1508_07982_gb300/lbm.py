@@ -58,6 +58,7 @@ class Desc(ctypes.Structure):
         ("spheres", (ctypes.c_double * 4) * 64),
         ("n_regions", ctypes.c_int32),
         ("regions", (ctypes.c_double * 8) * 64),
+        ("u_shift", ctypes.c_double * 3),
     ]
 
 
@@ -208,6 +209,8 @@ def make_desc(case, precision="fp64"):
             vals = [1.0, float(r[1])] + [float(v) for v in r[2]] + [float(r[3]), 0.0, 0.0]
         for k in range(8):
             d.regions[i][k] = vals[k]
+    for a, v in enumerate(case.get("u_shift", (0.0, 0.0, 0.0))):
+        d.u_shift[a] = float(v)
     return d
 
 

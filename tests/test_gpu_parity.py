@@ -269,8 +269,14 @@ def test_stepping_one_at_a_time_equals_stepping_in_one_call(lbm):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32s", "fp16s"])
-def test_checkpoint_resume_is_bit_exact(lbm, precision):
-    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True)
+@pytest.mark.parametrize("shift", [False, True])
+def test_checkpoint_resume_is_bit_exact(lbm, precision, shift):
+    """lbm_get_pdfs / lbm_set_pdfs round trip, then 4 more coarse steps on both forests.  FP64,
+    and the shifted layouts with the f - w rho0 shift, resume bit for bit.  With a storage shift
+    by f^eq(rho0, u0) an FP32 stored value below about 2e-9 can lose low bits in the FP64 f it is
+    read out as (f = v + f^eq then needs more than 53 bits): the resumed run then agrees to a few
+    FP32 units in the last place, 1e-7 (FP16 values are never that small: exact)."""
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True, shift=shift)
     a = lbm.Forest(case, precision=precision)
     a.init_uniform(case["u_init"])
     a.step_coarse(3)
@@ -281,7 +287,12 @@ def test_checkpoint_resume_is_bit_exact(lbm, precision):
     a.step_coarse(4)
     b.step_coarse(4)
     for L in range(a.nlev):
-        assert np.array_equal(a.get_pdfs(L), b.get_pdfs(L), equal_nan=True)
+        pa, pb = a.get_pdfs(L), b.get_pdfs(L)
+        if shift and precision == "fp32s":
+            assert (np.isnan(pa) == np.isnan(pb)).all()
+            assert np.nanmax(np.abs(pa - pb)) <= 1e-7
+        else:
+            assert np.array_equal(pa, pb, equal_nan=True)
 
 
 def test_reduced_precision_errors_against_the_fp64_oracle(lbm, oracle_mod):
