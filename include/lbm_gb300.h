@@ -48,7 +48,7 @@ typedef enum {
     LBM_ENONFINITE = 6    /* a reduction met a NaN or Inf */
 } lbm_status;
 
-typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_NOSLIP = 1, LBM_BC_VELOCITY = 2 } lbm_bc;
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_NOSLIP = 1, LBM_BC_VELOCITY = 2, LBM_BC_FREESLIP = 3 } lbm_bc;
 typedef enum { LBM_SRT = 0, LBM_TRT = 1 } lbm_collision;
 
 /* PDF storage.  FP64 stores f_a; FP32S and FP16S store the shifted value f_a - w_a rho0 and
@@ -64,7 +64,15 @@ typedef enum { LBM_FP64 = 0, LBM_FP32S = 1, LBM_FP16S = 2 } lbm_precision;
  *   root_blocks   number of root blocks per axis (>= 1)
  *   block_cells   B, cells per block edge on every level: 8, 16 or 32
  *   max_level     deepest level a split may create (0 .. LBM_MAX_LEVELS-1)
- *   bc[6]         faces x-, x+, y-, y+, z-, z+; periodic faces come in pairs
+ *   bc[6]         faces x-, x+, y-, y+, z-, z+; periodic faces come in pairs.  Free-slip
+ *                 (named only, Sec. 4.2) is read as specular reflection: the value entering a
+ *                 cell across the face is the one its tangential neighbour sent towards the
+ *                 face, with the normal component of the direction reversed; beyond several
+ *                 faces, the first non-free-slip face in the order z+, z-, y+, y-, x+, x-
+ *                 applies, or, if all are free-slip, the reflection in each (an obstacle at
+ *                 the mirrored cell bounces the value back instead).  Every leaf touching a
+ *                 free-slip face must be of one level (no level interface meets the face):
+ *                 lbm_plan_create / lbm_create_forest return LBM_EINVAL otherwise.
  *   bc_velocity   wall velocity of LBM_BC_VELOCITY faces (Sec. 5.2: velocity bounce-back)
  *   rho0          reference density of the incompressible equilibrium (Eq. fequ)
  *   spheres       no-slip obstacles (cx, cy, cz, r): a cell whose centre lies inside

@@ -29,7 +29,12 @@
  *    covered by the finer level; the mean of the 8 children of x is summed
  *    pairwise ((c0+c1)+(c2+c3))+((c4+c5)+(c6+c7)), children in z-y-x bit order;
  *  - a cell outside the domain takes the boundary condition of the first face
- *    it lies beyond in the order z+, z-, y+, y-, x+, x-;
+ *    it lies beyond in the order z+, z-, y+, y-, x+, x-, skipping free-slip faces;
+ *    a cell beyond free-slip faces only is their mirror: for a direction a whose
+ *    target streams it holds the value of the mirror cell (one step back inside
+ *    along each of those faces' normals) in direction a with those normal
+ *    components negated (specular reflection; free-slip is named only, Sec. 4.2),
+ *    or the bounced value when the mirror cell is an obstacle;
  *  - cells covered by a coarser leaf take the flag of the covering coarse cell,
  *    which makes fluid/obstacle marking consistent across interfaces (Sec. 4.1).
  * Every cell that is not an owned fluid cell starts as NaN, so any read of a
@@ -50,11 +55,11 @@
 #define ORC_MAXREG 64
 #define PAD 5
 
-enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_VELOCITY = 2 };
+enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_VELOCITY = 2, BC_FREESLIP = 3 };
 enum { COLL_SRT = 0, COLL_TRT = 1 };
 enum { CLS_OUT = 0, CLS_OWNED = 1, CLS_G1 = 2, CLS_G2 = 3, CLS_G3 = 4, CLS_G4 = 5,
        CLS_FINER = 6, CLS_FAR = 7 };
-enum { FL_FLUID = 0, FL_NOSLIP = 1, FL_VEL = 2 };
+enum { FL_FLUID = 0, FL_NOSLIP = 1, FL_VEL = 2, FL_FREE = 3 };
 enum { ST_ABSENT = 0, ST_LEAF = 1, ST_SPLIT = 2 };
 
 typedef int (*orc_refine_fn)(int level, int bx, int by, int bz, void *user);
@@ -81,7 +86,8 @@ typedef struct {
     long ncell;
     double *f, *tmp;   /* [ncell][Q] */
     unsigned char *cls, *flag, *inS;
-    signed char *vface;            /* wall face of velocity cells, else -1 */
+    signed char *vface;            /* wall face of velocity cells; mirrored axes (bits) of
+                                      free-slip cells; else -1 */
     long *C; long nC;              /* owned fluid cells: collide set */
     long *S; long nS;              /* owned, G1, G2 fluid cells: stream set */
     long *G; long *Gp; long nG;    /* G1..G4 cells and their parent index on L-1 */
@@ -448,14 +454,18 @@ static int classify(orc *o, int L) {
         for (int a = 0; a < 3; a++) if (g[a] < 0 || g[a] >= V->N[a]) out = 1;
         if (out) {
             V->cls[c] = CLS_OUT;
+            V->flag[c] = FL_FREE;
+            int axes = 0;
             for (int k = 0; k < 6; k++) {
                 int fce = face_order[k], a = fce / 2;
                 int beyond = (fce & 1) ? (g[a] >= V->N[a]) : (g[a] < 0);
                 if (!beyond) continue;
+                if (o->d.bc[fce] == BC_FREESLIP) { axes |= 1 << a; continue; }
                 if (o->d.bc[fce] == BC_VELOCITY) { V->flag[c] = FL_VEL; V->vface[c] = (signed char)fce; }
                 else V->flag[c] = FL_NOSLIP;
                 break;
             }
+            if (V->flag[c] == FL_FREE) V->vface[c] = (signed char)axes;
             dist[c] = 255;
             continue;
         }
@@ -606,6 +616,20 @@ static void op_boundary(orc *o, int L) {
             long nn = nbr(o, V, x, y, z, EV[a][0], EV[a][1], EV[a][2]);
             if (nn < 0 || !V->inS[nn]) continue;
             double v = V->f[nn * Q + OPP[a]];
+            if (V->flag[b] == FL_FREE) {
+                /* specular reflection: the mirror cell one step back inside along each mirrored
+                 * normal, direction a with those components negated */
+                int axes = V->vface[b], d[3] = {0, 0, 0}, e[3];
+                for (int k = 0; k < 3; k++) {
+                    e[k] = EV[a][k];
+                    if (axes >> k & 1) { d[k] = EV[a][k]; e[k] = -EV[a][k]; }
+                }
+                long m = nbr(o, V, x, y, z, d[0], d[1], d[2]);
+                int am = 0;
+                for (int k = 1; k < Q; k++)
+                    if (EV[k][0] == e[0] && EV[k][1] == e[1] && EV[k][2] == e[2]) am = k;
+                if (m >= 0 && V->flag[m] == FL_FLUID) v = V->f[m * Q + am];
+            }
             if (V->flag[b] == FL_VEL) {
                 const double *uw = o->d.bcu[(int)V->vface[b]];
                 v += 6.0 * W[a] * o->d.rho0 * (EV[a][0] * uw[0] + EV[a][1] * uw[1] + EV[a][2] * uw[2]);

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liblbm_oracle.so")
 
-_BC = {"periodic": 0, "noslip": 1, "velocity": 2}
+_BC = {"periodic": 0, "noslip": 1, "velocity": 2, "freeslip": 3}
 _COLL = {"srt": 0, "trt": 1}
 
 CLS_OUT, CLS_OWNED, CLS_G1, CLS_G2, CLS_G3, CLS_G4, CLS_FINER, CLS_FAR = range(8)

@@ -333,17 +333,45 @@ struct Builder {
         return g;
     }
 
-    // Wall face whose boundary condition a source beyond the domain takes: the first face it
-    // lies beyond in the order z+, z-, y+, y-, x+, x-.
+    // Wall face whose boundary condition a source beyond the domain takes: the first non-free-
+    // slip face it lies beyond in the order z+, z-, y+, y-, x+, x-; -1 when every face it lies
+    // beyond is free-slip (the source is then mirrored).
     int wall_face(const HostLevel& V, int k, int sx, int sy, int sz) const {
         const int B = p.B;
         const int g[3] = {V.pos[3 * k] * B + sx, V.pos[3 * k + 1] * B + sy, V.pos[3 * k + 2] * B + sz};
-        if (!p.per[2] && g[2] >= V.N[2]) return 5;
-        if (!p.per[2] && g[2] < 0) return 4;
-        if (!p.per[1] && g[1] >= V.N[1]) return 3;
-        if (!p.per[1] && g[1] < 0) return 2;
-        if (!p.per[0] && g[0] >= V.N[0]) return 1;
-        return 0;
+        for (int f = 5; f >= 0; f--) {
+            const int a = f >> 1;
+            const bool beyond = !p.per[a] && ((f & 1) ? g[a] >= V.N[a] : g[a] < 0);
+            if (beyond && p.d.bc[f] != LBM_BC_FREESLIP) return f;
+        }
+        return -1;
+    }
+
+    // Every leaf that touches a free-slip face has the same level, so that no level interface,
+    // and no ghost cell, meets the face (the reflection then only reads owned cells).
+    bool freeslip_faces_on_one_level(std::string& err) const {
+        for (int f = 0; f < 6; f++) {
+            if (p.d.bc[f] != LBM_BC_FREESLIP) continue;
+            const int a = f >> 1;
+            int seen = -1;
+            for (int L = 0; L < p.nlev; L++) {
+                const int n[3] = {p.lv[L].nb[0], p.lv[L].nb[1], p.lv[L].nb[2]};
+                const int side = (f & 1) ? n[a] - 1 : 0;
+                for (int z = 0; z < n[2]; z++)
+                    for (int y = 0; y < n[1]; y++)
+                        for (int x = 0; x < n[0]; x++) {
+                            const int c[3] = {x, y, z};
+                            if (c[a] != side || state(L, x, y, z) != LEAF) continue;
+                            if (seen >= 0 && seen != L) {
+                                err = "leaves of levels " + std::to_string(seen) + " and " + std::to_string(L) +
+                                      " touch free-slip face " + std::to_string(f) + " (a level interface meets it)";
+                                return false;
+                            }
+                            seen = L;
+                        }
+            }
+        }
+        return true;
     }
 
     // Fast-path bits of an owned cell's link mask m (Sec. 2.2, Eq. ftoc):
@@ -375,7 +403,8 @@ struct Builder {
                 bounce = false;
             } else if (nb == NB_WALL) {
                 const int f = wall_face(V, k, s[0], s[1], s[2]);
-                if (face == 7) face = f;
+                if (f < 0) bounce = false;           // free-slip reflection: general pull
+                else if (face == 7) face = f;
                 else if (face != f) bounce = false;
             } else if (nb >= 0 && V.cell[size_t(nb) * B3 + ((size_t(s[2] & M) * B + (s[1] & M)) * B) + (s[0] & M)] == CK_SOLID) {
                 solid_seen = true;
@@ -383,7 +412,7 @@ struct Builder {
                 bounce = false;
             }
         }
-        if (bounce && solid_seen && face != 7 && p.d.bc[face] == LBM_BC_VELOCITY) bounce = false;
+        if (bounce && solid_seen && face != 7 && p.d.bc[face] == LBM_BC_VELOCITY) bounce = false;   // two terms
         uint32_t r = 0;
         if (bounce) r |= (1u << 29) | (uint32_t(face) << 25);
         if (coal_all) r |= 1u << 28;
@@ -513,6 +542,10 @@ struct Builder {
                     source(V, k, x, y, z, q, nb, sc);
                     if ((gl >> q) & 1u) {
                         const bool bounce = nb == NB_WALL || (nb >= 0 && V.cell[sc] == CK_SOLID);
+                        if (nb == NB_WALL && wall_face(V, k, x - EX[q], y - EY[q], z - EZ[q]) < 0) {
+                            err = "a ghost cell meets a free-slip face";
+                            return false;
+                        }
                         if (!bounce) {
                             err = "a needed ghost value has no source within ghost layer 3";
                             return false;
@@ -594,7 +627,7 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
             return false;
         }
         for (int s = 0; s < 2; s++)
-            if (d->bc[2 * a + s] < LBM_BC_PERIODIC || d->bc[2 * a + s] > LBM_BC_VELOCITY) {
+            if (d->bc[2 * a + s] < LBM_BC_PERIODIC || d->bc[2 * a + s] > LBM_BC_FREESLIP) {
                 err = "unknown boundary condition";
                 return false;
             }
@@ -611,6 +644,7 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
     }
     Builder b{p, refine, flag, user};
     if (!b.leaves(err)) return false;
+    if (!b.freeslip_faces_on_one_level(err)) return false;
     for (int L = 0; L < p.nlev; L++)
         if (!b.bricks(L, err)) return false;
     for (int L = 0; L < p.nlev; L++) b.children(L);

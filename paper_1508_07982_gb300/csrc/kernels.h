@@ -49,6 +49,7 @@ struct StepArgs {
     int lzc;              // log2 of the cells each thread walks along z
     int minb;             // CTAs per SM the kernel variant is compiled for (2, 3 or 4)
     int per;              // bit a set: axis a periodic
+    int fslip;            // bit f set: face f (x-, x+, y-, y+, z-, z+) is free-slip
     const LevelParams* params;
     const double* wall;   // [8][19] bounce-back terms 6 w_a rho0 (e_a . (u_w - u0)): faces 0-5,
                           // row 7 obstacles (u_w = 0), row 6 unused

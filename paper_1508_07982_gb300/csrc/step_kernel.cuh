@@ -227,8 +227,9 @@ template <> struct Par<float> {
 // links the link mask routes here:
 //   - coalescence (owned cells only): mean of the 8 finer children of x (Eq. ftoc);
 //   - obstacle or domain wall: bounce-back of the cell's own opposite value (Sec. 2.2), plus
-//     6 w rho0 e.(u_w - u0) (u_w = 0 except on velocity walls, u0 the storage shift); a source
-//     beyond several faces takes the first of
+//     6 w rho0 e.(u_w - u0) (u_w = 0 except on velocity walls, u0 the storage shift), or the
+//     specular reflection of free-slip faces; a source beyond several faces takes the first
+//     non-free-slip face of
 //     z+, z-, y+, y-, x+, x-.  A ghost cell's own value in sub-step 1 is the exploded one;
 //   - otherwise the value of the source cell: stored (owned, or ghost layers 1-2 after their
 //     sub-step-1 stream), or exploded (ghost layers in sub-step 1, layer 3 always).
@@ -267,14 +268,48 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     }
     if (nb == NB_WALL) {
         const int* P = a.lv.pos + 3 * brick;
-        const int gx = P[0] * B + sx, gy = P[1] * B + sy, gz = P[2] * B + sz;
-        int face;
-        if (!(a.per & 4) && gz >= a.lv.N[2]) face = 5;
-        else if (!(a.per & 4) && gz < 0) face = 4;
-        else if (!(a.per & 2) && gy >= a.lv.N[1]) face = 3;
-        else if (!(a.per & 2) && gy < 0) face = 2;
-        else if (!(a.per & 1) && gx >= a.lv.N[0]) face = 1;
-        else face = 0;
+        const int g[3] = {P[0] * B + sx, P[1] * B + sy, P[2] * B + sz};
+        // the first non-free-slip face the source lies beyond, in the order z+, z-, y+, y-, x+, x-
+        int face = -1, mirror = 0;
+        for (int f = 5; f >= 0; f--) {
+            const int ax = f >> 1;
+            if ((a.per >> ax) & 1) continue;
+            if (!((f & 1) ? g[ax] >= a.lv.N[ax] : g[ax] < 0)) continue;
+            if ((a.fslip >> f) & 1) {
+                mirror |= 1 << ax;
+            } else {
+                face = f;
+                break;
+            }
+        }
+        if (face < 0 && owned) {
+            // every face is free-slip: specular reflection.  The value comes from the tangential
+            // neighbour (the source moved back inside along the mirrored axes), in direction q
+            // with those components reversed; an obstacle there bounces it back instead.  The
+            // neighbour is an owned cell of this level (no level interface meets a free-slip face).
+            const int mx = (mirror & 1) ? x : sx, my = (mirror & 2) ? y : sy, mz = (mirror & 4) ? z : sz;
+            const int mox = mx < 0 ? -1 : (mx > M ? 1 : 0);
+            const int moy = my < 0 ? -1 : (my > M ? 1 : 0);
+            const int moz = mz < 0 ? -1 : (mz > M ? 1 : 0);
+            const int mb = (mox | moy | moz) ? __ldg(nbr + 13 + mox + 3 * moy + 9 * moz) : brick;
+            const int rx = (mirror & 1) ? -ex : ex, ry = (mirror & 2) ? -ey : ey, rz = (mirror & 4) ? -ez : ez;
+            int qm = q;
+#pragma unroll
+            for (int k = 1; k < 19; k++)
+                if (dex(k) == rx && dey(k) == ry && dez(k) == rz) qm = k;
+            if (mb >= 0) {
+                const int64_t midx = (int64_t(mb) << B3s) + ((mz & M) << (2 * LB)) + ((my & M) << LB) + (mx & M);
+                if (__ldg(a.lv.cell + midx) != CK_SOLID) {
+                    // the shifted layouts store f - f^eq(rho0, u0): f^eq_qm - f^eq_q of the shift is
+                    // w rho0 (1.5 (E' - E) + 1.125 (E'^2 - E^2)) with E = 2 e_q.u0, E' = 2 e_qm.u0
+                    const float E = a.e_two_u0[q], Em = a.e_two_u0[qm];
+                    return acc.load(src, n, qm, midx) +
+                           C(float(dw(q)) * float(a.rho0) * (1.5f * (Em - E) + 1.125f * (Em * Em - E * E)));
+                }
+            }
+            face = 7;   // obstacle at the mirrored cell: bounce-back, obstacle term
+        }
+        if (face < 0) face = 7;   // not reached: ghost cells never meet a free-slip face
         const C o = own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
         return o + C(__ldg(a.wall + face * 19 + q));
     }

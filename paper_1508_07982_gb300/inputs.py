@@ -131,6 +131,19 @@ def pipe_poiseuille_case(D=60, B=8, lmax=0, where="wall", lambda_e0=0.6, accel=1
     return case, refine, flag, (c, R)
 
 
+def freeslip_box_case(n=32, B=8, refine=True, lid=None, spheres=(), collision="trt", omega=1.6):
+    """Box of n^3 level-0 cells, periodic in x, free-slip on the y and z faces (or the z+ face a
+    velocity lid moving along x when lid is given); with refine, the central (n/4 .. 3n/4)^3 region
+    (whole blocks, away from every face) is refined once.  Free-slip faces are named only in the
+    paper (Sec. 4.2)."""
+    r = n // B
+    bc = ["periodic", "periodic", "freeslip", "freeslip", "freeslip", "velocity" if lid else "freeslip"]
+    bc_u = [(0.0, 0.0, 0.0)] * 5 + [(lid or 0.0, 0.0, 0.0)]
+    regions = [("box", 1, (n / 4 + 1, n / 4 + 1, n / 4 + 1), (3 * n / 4 - 1, 3 * n / 4 - 1, 3 * n / 4 - 1))] if refine else []
+    return dict(root=(r, r, r), B=B, lmax=1 if refine else 0, collision=collision, rho0=1.0, bc=bc, bc_u=bc_u,
+                spheres=list(spheres), regions=regions, lambda_e0=omega, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0))
+
+
 def batch_cases(n=256, seed=SEED, B=16):
     """Small lid-driven cavities for stepping many forests together (the batched workload).
 

@@ -17,7 +17,7 @@ Q = 19
 
 LBM_OK, LBM_EINVAL, LBM_EUNBALANCED, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENONFINITE = range(7)
 PRECISION = {"fp64": 0, "fp32s": 1, "fp16s": 2}
-_BC = {"periodic": 0, "noslip": 1, "velocity": 2}
+_BC = {"periodic": 0, "noslip": 1, "velocity": 2, "freeslip": 3}
 _COLL = {"srt": 0, "trt": 1}
 
 # Every entry point of include/lbm_gb300.h (checked by the tests).

@@ -59,6 +59,7 @@ def _cases():
     yield "channel", inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5), inlet_outlet=True), None
     yield "poiseuille", inputs.plane_poiseuille_case(B=8, where="both"), None
     yield "lid-scaling", inputs.lid_scaling_case(roots=(3, 1, 3), B=8), None
+    yield "free-slip", inputs.freeslip_box_case(lid=0.02, spheres=[(8.0, 1.0, 16.0, 4.0), (16.0, 16.0, 16.0, 2.5)]), None
     yield "periodic-ball", inputs.periodic_case(n=64, B=8, collision="trt", omega=1.7,
                                                 regions=[("ball", 3, (5, 60, 33), 9.0)], lmax=3), None
     rng = np.random.default_rng(7)
@@ -76,7 +77,7 @@ def _cases():
                          regions=[]), refine
 
 
-@pytest.mark.parametrize("name", ["cavity", "channel", "poiseuille", "lid-scaling", "periodic-ball", "random"])
+@pytest.mark.parametrize("name", ["cavity", "channel", "poiseuille", "lid-scaling", "free-slip", "periodic-ball", "random"])
 def test_host_planner_matches_the_oracle_forest(lbm, oracle_mod, name):
     case, refine = next((c, r) for n, c, r in _cases() if n == name)
     memo = {}
@@ -131,3 +132,14 @@ def test_lid_scaling_forest_reproduces_the_benchmark_level_table(lbm, roots, B):
         assert np.abs(got[key] - np.array(ref)).max() <= 0.01 + 1e-9, (key, got[key], ref)
     # every leaf holds B^3 fluid cells (no obstacles)
     assert sum(p.counts(L)["fluid"] for L in range(4)) == int(n.sum()) * B ** 3
+
+
+def test_a_level_interface_on_a_free_slip_face_is_rejected(lbm):
+    """Free-slip reflection reads the tangential neighbour on the same level, so every leaf that
+    touches a free-slip face must have one level; the planner rejects forests where an interface
+    meets the face (here the refined box reaches the y- face)."""
+    case = dict(inputs.freeslip_box_case(), regions=[("box", 1, (0, 0, 0), (8, 8, 8))])
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.Plan(case)
+    assert ei.value.status == lbm.LBM_EINVAL and "free-slip face" in str(ei.value)
+    lbm.Plan(inputs.freeslip_box_case())            # the centre-refined box is accepted

@@ -525,3 +525,66 @@ def test_pipe_poiseuille_matches_the_paper_table(oracle_mod):
     want = _golden_pipe()[("global", 0)]
     for g, p in zip(got, want):
         assert abs(g - p) / p < 0.02, (got, want)
+
+
+# --------------------------------------------------------------------------- free-slip faces
+
+def test_uniform_flow_along_free_slip_walls_stays_uniform(oracle_mod):
+    """Specular reflection at free-slip faces (named only, Sec. 4.2) maps the equilibrium of a flow
+    parallel to the wall onto itself: a uniform flow along x in a box with free-slip y and z faces
+    (and a refined centre) stays uniform to round-off."""
+    o = oracle_mod.Oracle(inputs.freeslip_box_case())
+    assert o.nlev == 2
+    o.init_fields(inputs.uniform_field(u=(0.03, 0.0, 0.0)))
+    o.step(20)
+    for L in range(o.nlev):
+        rho, u = o.macro(L)
+        cls, flg = o.classes(L)
+        own = (cls == 1) & (flg == 0)
+        assert np.abs(u[0][own] - 0.03).max() < 1e-14
+        assert np.abs(u[1:, own]).max() < 1e-14 and np.abs(rho[own] - 1.0).max() < 1e-14
+
+
+def test_free_slip_walls_conserve_mass_and_tangential_momentum(oracle_mod):
+    """A reflected population keeps its mass and its tangential momentum: with free-slip y and z
+    faces and periodic x, total mass and x momentum are conserved to round-off (y and z momentum
+    are not: the walls reverse normal components)."""
+    o = oracle_mod.Oracle(inputs.freeslip_box_case())
+    o.init_fields(inputs.taylor_green_field(32))
+    m0 = o.mass_momentum()
+    o.step(20)
+    m1 = o.mass_momentum()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-13
+    assert abs(m1[1] - m0[1]) / (0.02 * m0[0]) < 1e-12
+    assert np.abs(m1[2:] - m0[2:]).max() > 1e-6           # the normal components do change
+
+
+def test_shear_mode_between_free_slip_walls_decays_at_the_viscous_rate(oracle_mod):
+    """u_x = U cos(pi y / H) satisfies the free-slip condition du/dy = 0 at both walls (halfway
+    between the wall layer and its mirror), so it decays as exp(-nu (pi/H)^2 t) with
+    nu = (1/lambda_e - 1/2)/3; measured between steps 100 and 300 (after the start transient)."""
+    H, U, le = 32, 1e-3, 1.2
+    case = dict(root=(1, H // 8, 1), B=8, lmax=0, collision="srt", rho0=1.0,
+                bc=["periodic", "periodic", "freeslip", "freeslip", "periodic", "periodic"], bc_u=[(0, 0, 0)] * 6,
+                spheres=[], regions=[], lambda_e0=le, magic=3 / 16, accel=(0, 0, 0))
+
+    def field(L, X, Y, Z):
+        return 1.0, (U * np.cos(math.pi * (Y + 0.5) / H), 0 * Y, 0 * Y)
+
+    o = oracle_mod.Oracle(case)
+    o.init_fields(field)
+    X, Y, Z = o.coords(0)
+    cls, flg = o.classes(0)
+    own = (cls == 1) & (flg == 0)
+    mode = np.cos(math.pi * (Y[own] + 0.5) / H)
+
+    def amplitude():
+        return (o.macro(0)[1][0][own] * mode).sum() / (mode * mode).sum()
+
+    o.step(100)
+    a1 = amplitude()
+    o.step(200)
+    a2 = amplitude()
+    nu = (1 / le - 0.5) / 3
+    rate = -math.log(a2 / a1) / 200
+    assert abs(rate / (nu * (math.pi / H) ** 2) - 1) < 5e-3
