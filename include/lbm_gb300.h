@@ -65,7 +65,7 @@ typedef enum { LBM_FP64 = 0, LBM_FP32S = 1, LBM_FP16S = 2 } lbm_precision;
  *   block_cells   B, cells per block edge on every level: 8, 16 or 32
  *   max_level     deepest level a split may create (0 .. LBM_MAX_LEVELS-1)
  *   bc[6]         faces x-, x+, y-, y+, z-, z+; periodic faces come in pairs.  Free-slip
- *                 (named only, Sec. 4.2) is read as specular reflection: the value entering a
+ *                 (named only, Sec. 4.1) is read as specular reflection: the value entering a
  *                 cell across the face is the one its tangential neighbour sent towards the
  *                 face, with the normal component of the direction reversed; beyond several
  *                 faces, the first non-free-slip face in the order z+, z-, y+, y-, x+, x-

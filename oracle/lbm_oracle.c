@@ -33,7 +33,7 @@
  *    a cell beyond free-slip faces only is their mirror: for a direction a whose
  *    target streams it holds the value of the mirror cell (one step back inside
  *    along each of those faces' normals) in direction a with those normal
- *    components negated (specular reflection; free-slip is named only, Sec. 4.2),
+ *    components negated (specular reflection; free-slip is named only, Sec. 4.1),
  *    or the bounced value when the mirror cell is an obstacle;
  *  - cells covered by a coarser leaf take the flag of the covering coarse cell,
  *    which makes fluid/obstacle marking consistent across interfaces (Sec. 4.1).

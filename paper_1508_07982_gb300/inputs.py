@@ -135,7 +135,7 @@ def freeslip_box_case(n=32, B=8, refine=True, lid=None, spheres=(), collision="t
     """Box of n^3 level-0 cells, periodic in x, free-slip on the y and z faces (or the z+ face a
     velocity lid moving along x when lid is given); with refine, the central (n/4 .. 3n/4)^3 region
     (whole blocks, away from every face) is refined once.  Free-slip faces are named only in the
-    paper (Sec. 4.2)."""
+    paper (Sec. 4.1)."""
     r = n // B
     bc = ["periodic", "periodic", "freeslip", "freeslip", "freeslip", "velocity" if lid else "freeslip"]
     bc_u = [(0.0, 0.0, 0.0)] * 5 + [(lid or 0.0, 0.0, 0.0)]

@@ -530,7 +530,7 @@ def test_pipe_poiseuille_matches_the_paper_table(oracle_mod):
 # --------------------------------------------------------------------------- free-slip faces
 
 def test_uniform_flow_along_free_slip_walls_stays_uniform(oracle_mod):
-    """Specular reflection at free-slip faces (named only, Sec. 4.2) maps the equilibrium of a flow
+    """Specular reflection at free-slip faces (named only, Sec. 4.1) maps the equilibrium of a flow
     parallel to the wall onto itself: a uniform flow along x in a box with free-slip y and z faces
     (and a refined centre) stays uniform to round-off."""
     o = oracle_mod.Oracle(inputs.freeslip_box_case())
