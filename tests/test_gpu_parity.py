@@ -442,10 +442,11 @@ def _mirror_gap(f, level, axis, n0=(256, 64, 64)):
 
 
 def test_recorded_totals_with_obstacle_warps_and_a_new_launch_configuration(lbm):
-    """The bench workload (FP32S): on the finest level whole warps lie inside the sphere and
-    record nothing, so their totals entries must stay zero, also after a new launch configuration
-    moves the warp layout.  The recorded totals (moments the last collisions started from) and the
-    stored state's totals agree to FP32 rounding; a stale warp entry would add tens of cells."""
+    """The bench workload (FP32S): on the finest level whole warps lie inside the sphere (they
+    record zero moments), and a new launch configuration changes the number and layout of the
+    warp entries.  The recorded totals (moments the last collisions started from) and the stored
+    state's totals agree to FP32 rounding; a stale or missing warp entry would add or drop tens of
+    cells."""
     case = inputs.sphere_channel_case()
     f = lbm.Forest(case, precision="fp32s")
     f.init_uniform(case["u_init"])
