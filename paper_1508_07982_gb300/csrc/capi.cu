@@ -214,6 +214,7 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.fslip = 0;
     for (int k = 0; k < 6; k++)
         if (f->plan.d.bc[k] == LBM_BC_FREESLIP) a.fslip |= 1 << k;
+    a.obstacle_term = (f->u0[0] != 0.0 || f->u0[1] != 0.0 || f->u0[2] != 0.0) ? 1 : 0;
     for (int k = 0; k < 3; k++) a.two_u0[k] = float(2.0 * f->u0[k]);
     for (int q = 0; q < Q; q++) a.e_two_u0[q] = float(2.0 * (EX[q] * f->u0[0] + EY[q] * f->u0[1] + EZ[q] * f->u0[2]));
     return a;

@@ -55,6 +55,7 @@ struct StepArgs {
                           // row 7 obstacles (u_w = 0), row 6 unused
     double rho0, inv_rho0;
     double* totals;       // per-warp post-streaming moments of the owned cells, or NULL
+    int obstacle_term;    // 1: obstacle bounce-backs add wall row 7 (a nonzero storage shift)
     float two_u0[3];      // 2 u0 and 2 e_a . u0 of the storage shift (FP32 arithmetic; 0 unshifted)
     float e_two_u0[19];
 };

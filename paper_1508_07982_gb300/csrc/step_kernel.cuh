@@ -259,9 +259,11 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
     if (nb >= 0) {
         const int64_t sidx = (int64_t(nb) << B3s) + ((sz & M) << (2 * LB)) + ((sy & M) << LB) + (sx & M);
         const uint8_t ck = __ldg(a.lv.cell + sidx);
-        if (ck == CK_SOLID)
-            return (own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx)) +
-                   C(__ldg(a.wall + 7 * 19 + q));
+        if (ck == CK_SOLID) {
+            C t = own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
+            if (a.obstacle_term) t += C(__ldg(a.wall + 7 * 19 + q));
+            return t;
+        }
         if (ck == CK_FAR) return qnan<C>();   // never a source: layer 4+ holds no value
         if (nb >= a.lv.nown && (a.substep == 1 || ck == CK_G3)) return acc.coarse(nb, sx & M, sy & M, sz & M, q);
         return acc.load(src, n, q, sidx);
@@ -271,15 +273,25 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
         const int g[3] = {P[0] * B + sx, P[1] * B + sy, P[2] * B + sz};
         // the first non-free-slip face the source lies beyond, in the order z+, z-, y+, y-, x+, x-
         int face = -1, mirror = 0;
-        for (int f = 5; f >= 0; f--) {
-            const int ax = f >> 1;
-            if ((a.per >> ax) & 1) continue;
-            if (!((f & 1) ? g[ax] >= a.lv.N[ax] : g[ax] < 0)) continue;
-            if ((a.fslip >> f) & 1) {
-                mirror |= 1 << ax;
-            } else {
-                face = f;
-                break;
+        if (!a.fslip) {
+            if (!(a.per & 4) && g[2] >= a.lv.N[2]) face = 5;
+            else if (!(a.per & 4) && g[2] < 0) face = 4;
+            else if (!(a.per & 2) && g[1] >= a.lv.N[1]) face = 3;
+            else if (!(a.per & 2) && g[1] < 0) face = 2;
+            else if (!(a.per & 1) && g[0] >= a.lv.N[0]) face = 1;
+            else face = 0;
+        } else {
+#pragma unroll
+            for (int f = 5; f >= 0; f--) {
+                const int ax = f >> 1;
+                if ((a.per >> ax) & 1) continue;
+                if (!((f & 1) ? g[ax] >= a.lv.N[ax] : g[ax] < 0)) continue;
+                if ((a.fslip >> f) & 1) {
+                    mirror |= 1 << ax;
+                } else {
+                    face = f;
+                    break;
+                }
             }
         }
         if (face < 0 && owned) {
@@ -407,7 +419,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
 #pragma unroll
                 for (int q = 1; q < 19; q++)
                     if ((mq >> q) & 1u) {
-                        v[q] = C(Store<T>::ld(p + int64_t(dopp(q)) * n)) + C(__ldg(a.wall + face * 19 + q));
+                        C t = C(Store<T>::ld(p + int64_t(dopp(q)) * n));
+                        if (face != 7 || a.obstacle_term) t += C(__ldg(a.wall + face * 19 + q));
+                        v[q] = t;
                     }
             } else if (m & LINK_COAL_ONLY) {
 #pragma unroll
