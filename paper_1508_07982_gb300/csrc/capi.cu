@@ -65,6 +65,7 @@ struct DevBuf {
     uint8_t* colspec = nullptr;
     uint32_t* gwork[2] = {nullptr, nullptr};
     uint32_t* ework = nullptr;
+    uint32_t* cwork = nullptr;
     double* wpart = nullptr;   // per-warp moments of the level's last sub-step
 };
 
@@ -236,7 +237,7 @@ void build_schedule(lbm_forest* f) {
         while (lzc > 0 && int64_t(V.nown) * B * B * (B >> lzc) / 256 < int64_t(4) * sms * f->minb) lzc--;
         const int64_t units = int64_t(V.nown) * B * B * (B >> lzc);
         const int64_t nwork = int64_t(V.gwork[s - 1].size() / 4);
-        int grid = int((units + 255) / 256) + int((nwork + 255) / 256);
+        int grid = int((units + 255) / 256) + int((nwork + 255) / 256) + int((V.cwork.size() + 255) / 256);
         f->sched.push_back({L, s, grid, 0, lzc});
     };
     auto explode = [&](int L) {
@@ -266,7 +267,8 @@ void build_schedule(lbm_forest* f) {
                 Launch& l = f->sched[k];
                 l.tot = 1;
                 const int64_t units = int64_t(f->plan.lv[L].nown) * B * B * (B >> l.lzc);
-                f->tot_warps[L] = units / 32;   // the warps with work: entries 0 .. units/32 - 1
+                // the column walk's warps (units / 32), then the coupled cells' warps
+                f->tot_warps[L] = units / 32 + int64_t(f->plan.lv[L].cwork.size() + 255) / 256 * 8;
                 break;
             }
 }
@@ -434,6 +436,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
         cudaFree(b.gwork[0]);
         cudaFree(b.gwork[1]);
         cudaFree(b.ework);
+        cudaFree(b.cwork);
         cudaFree(b.wpart);
     }
     for (double* p : f->uprev) cudaFree(p);
@@ -489,10 +492,12 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
             (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.kind, V.kind)) ||
             (s = upload(&b.link, V.link)) || (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.colspec, V.colspec)) ||
             (s = upload(&b.gwork[0], V.gwork[0])) || (s = upload(&b.gwork[1], V.gwork[1])) ||
-            (s = upload(&b.ework, V.ework)))
+            (s = upload(&b.ework, V.ework)) || (s = upload(&b.cwork, V.cwork)))
             return bail(s);
-        // per-warp totals of the recording launch, sized for one cell per thread (the most warps)
-        if (cudaMalloc(&b.wpart, size_t((int64_t(V.nown) * B3 + 255) / 256 * 8 + 1) * 4 * sizeof(double)) != cudaSuccess)
+        // per-warp totals of the recording launch, sized for one cell per thread (the most warps),
+        // then the coupled cells' warps
+        const int64_t wmax = (int64_t(V.nown) * B3 + 255) / 256 * 8 + int64_t(V.cwork.size() + 255) / 256 * 8;
+        if (cudaMalloc(&b.wpart, size_t(wmax + 1) * 4 * sizeof(double)) != cudaSuccess)
             return bail(fail(LBM_ENOMEM, "cannot allocate the totals of level %d", L));
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -508,6 +513,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         g.colspec = b.colspec;
         g.ework = reinterpret_cast<const uint4*>(b.ework);
         g.nework = int(V.ework.size() / 4);
+        g.cwork = b.cwork;
+        g.ncwork = int(V.cwork.size());
         for (int k = 0; k < 2; k++) {
             g.gwork[k] = reinterpret_cast<const uint4*>(b.gwork[k]);
             g.ngwork[k] = int(V.gwork[k].size() / 4);
@@ -1076,7 +1083,8 @@ lbm_status build_phases(lbm_batch* b) {
                     grid = int((V.ework.size() / 4 + 255) / 256);
                 } else {
                     const int64_t units = int64_t(V.nown) * B * B * (B >> lzc[L]);
-                    grid = int((units + 255) / 256) + int((V.gwork[s - 1].size() / 4 + 255) / 256);
+                    grid = int((units + 255) / 256) + int((V.gwork[s - 1].size() / 4 + 255) / 256) +
+                           int((V.cwork.size() + 255) / 256);
                 }
                 if (grid > 0) {
                     Launch l{L, s == 0 ? 0 : s, grid, s == 0 ? 1 : 0, lzc[L]};

@@ -435,6 +435,7 @@ struct Builder {
         V.link.assign(size_t(V.nown) * B3, 0u);
         V.colsolid.assign(size_t(V.nown) * B * B, 0u);
         V.colspec.assign(size_t(V.nown) * B * B, 0);
+        V.cwork.clear();
         for (int k = 0; k < V.nown; k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
@@ -445,6 +446,9 @@ struct Builder {
                         if (V.cell[c] != CK_FLUID) {
                             m |= 1u << 31;
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
+                        } else if (coal_bits(V, k, x, y, z)) {   // coupled: its own thread
+                            V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
+                            V.cwork.push_back(uint32_t(c));
                         }
                         V.link[c] = m;
                         if (m) V.colspec[size_t(k) * B * B + size_t(y) * B + x] = 1;

@@ -28,12 +28,15 @@ struct DevLevel {
     const uint8_t* kind;  // [nbricks]
     const uint32_t* link;    // [nown * B^3] per owned cell: bit q set = link q needs the general
                              // pull; bits 25-29 fast-path codes; bit 31 = not a fluid cell
-    const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = not a fluid cell
+    const uint32_t* colsolid;  // [nown * B^2] per owned column: bit z = skipped by the column walk
+                               // (not a fluid cell, or a coupled cell)
     const uint8_t* colspec;    // [nown * B^2] per owned column: 1 if any cell has a nonzero link mask
     const uint4* gwork[2];     // ghost stream work of sub-step 1 and 2: {cell, need, coarse, special}
     int ngwork[2];
     const uint4* ework;        // explosion work: {cell, directions, coarse parent cell, 0}
     int nework;
+    const uint32_t* cwork;     // coupled cells (owned fluid cells with a coalescence link)
+    int ncwork;
     int nown, nbricks;
     int64_t ncells;
     int N[3];

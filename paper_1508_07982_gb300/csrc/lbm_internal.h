@@ -45,7 +45,8 @@ struct HostLevel {
                                    // same-level load; bit 29 = every such link is a bounce-back
                                    // (bits 25-27: wall face of its wall term, 7 = none); bit 28 =
                                    // every such link is a coalescence link; bit 31 = not fluid
-    std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = not fluid
+    std::vector<uint32_t> colsolid;  // [nown * B^2] per column of an owned brick: bit z = the column
+                                     // walk skips the cell (not fluid, or a coupled cell)
     std::vector<uint8_t> colspec;    // [nown * B^2] 1 if any cell of the column has a nonzero link mask
     // Ghost stream work of sub-step s+1: 4 words per entry {cell, need, coarse, special}: the
     // directions of the cell whose value a later pull reads, those whose source value is the
@@ -54,6 +55,9 @@ struct HostLevel {
     // Explosion work: 4 words per entry {cell, directions, coarse parent cell, 0}: the ghost-layer-1
     // values that owned cells pull in sub-step 1, copied from the parent (Eq. ctof).
     std::vector<uint32_t> ework;
+    // Coupled cells: owned fluid cells with a coalescence link (Eq. ftoc), the only owned cells
+    // that read the finer level.  One cell index per entry, in cell order.
+    std::vector<uint32_t> cwork;
     int64_t nghost12 = 0;          // fluid cells of ghost layers 1-2
     int64_t nfluid = 0;            // owned fluid cells
     int nbricks() const { return nown + nghost; }

@@ -355,12 +355,73 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
     const int upb = (1 << B2s) << (LB - a.lzc);            // units (column chunks) per brick
     const int64_t owned_units = int64_t(a.lv.nown) * upb;
     const int64_t owned_ctas = (owned_units + 255) >> 8;
+    const int64_t coupled_ctas = (int64_t(a.lv.ncwork) + 255) >> 8;
     const T* src = static_cast<const T*>(a.lv.f[a.cur]);
     T* dst = static_cast<T*>(a.lv.f[a.cur ^ 1]);
     const int64_t n = a.lv.ncells;
     const Access<T, C> acc{a, LB, M};
     const int tid = threadIdx.x;
 
+    if (bid < coupled_ctas) {
+        // coupled cells (those with a coalescence link, which the column walk skips), first in the
+        // grid so that their longer dependent chains overlap the walk: one thread per cell, plain
+        // pulls as in the walk, the marked links through the general path, then the collision; the
+        // recording launch appends their moments, one entry per warp after the walk's entries
+        const int j = int(bid * 256 + tid);
+        const bool want_tot = a.totals != nullptr;
+        C mom[4] = {C(0), C(0), C(0), C(0)};
+        if (j < a.lv.ncwork) {
+            const int c = int(__ldg(a.lv.cwork + j));
+            const int brick = c >> B3s, local = c & ((1 << B3s) - 1);
+            const int x = local & M, y = (local >> LB) & M, z = local >> B2s;
+            const uint32_t mq = __ldg(a.lv.link + c) & LINK_ALL;
+            const int* nbr = a.lv.nbr + brick * 27;
+            C v[19];
+            v[0] = acc.load(src, n, 0, c);
+#pragma unroll
+            for (int q = 1; q < 19; q++) {
+                v[q] = C(0);
+                if (!((mq >> q) & 1u)) {   // plain: the source holds the value (stored, in the grid)
+                    const int sx = x - dex(q), sy = y - dey(q), sz = z - dez(q);
+                    const int ox = sx < 0 ? -1 : (sx > M ? 1 : 0);
+                    const int oy = sy < 0 ? -1 : (sy > M ? 1 : 0);
+                    const int oz = sz < 0 ? -1 : (sz > M ? 1 : 0);
+                    const int nb = (ox | oy | oz) ? __ldg(nbr + 13 + ox + 3 * oy + 9 * oz) : brick;
+                    const int sidx = (max(nb, 0) << B3s) + ((sz & M) << B2s) + ((sy & M) << LB) + (sx & M);
+                    v[q] = acc.load(src, n, q, sidx);
+                }
+            }
+            C(&buf)[19][256] = slow[0];
+            for (int q = 1; q < 19; q++)
+                if ((mq >> q) & 1u) buf[q][tid] = pull_general<T, C, LB>(a, acc, brick, x, y, z, q, true);
+#pragma unroll
+            for (int q = 1; q < 19; q++)
+                if ((mq >> q) & 1u) v[q] = buf[q][tid];
+            const LevelParams* P = a.params;
+            const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
+            collide<C, COLL>(v, Par<C>::le(P), Par<C>::lo(P), fa, C(a.rho0), C(a.inv_rho0), a.two_u0, a.e_two_u0,
+                             [&](C R, C jx, C jy, C jz) {
+                                 mom[0] = R;
+                                 mom[1] = jx;
+                                 mom[2] = jy;
+                                 mom[3] = jz;
+                             });
+            T* p = dst + c;
+#pragma unroll
+            for (int q = 0; q < 19; q++) Store<T>::st(p + int64_t(q) * n, v[q]);
+        }
+        if (want_tot) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                C t = mom[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+                if ((tid & 31) == 0) a.totals[((owned_units >> 5) + bid * 8 + (tid >> 5)) * 4 + k] = double(t);
+            }
+        }
+        return;
+    }
+    bid -= coupled_ctas;
     if (bid < owned_ctas) {
         const int64_t u = bid * 256 + tid;
         // totals of the state this launch writes (the level's last sub-step of a coarse step): the
@@ -522,9 +583,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
         }
         return;
     }
+    const int gs = a.substep - 1;
     // ghost layers 1-2: stream only, the directions the work entry needs; a source holding an
     // exploded value is read from the coarse parent, and bounce-back/wall links take the general pull
-    const int gs = a.substep - 1;
     const int i = int((bid - owned_ctas) * 256 + tid);
     if (i >= a.lv.ngwork[gs]) return;
     const uint4 e = __ldg(a.lv.gwork[gs] + i);
