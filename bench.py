@@ -115,11 +115,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _kernel_hash():
+def _kernel_hash(read=None):
+    """Hash of the step-kernel sources with comments and blank lines removed (a comment edit does
+    not change the kernel the counters were taken on)."""
     h = hashlib.sha256()
     for name in ("step_kernel.cuh", "kernels_impl.cuh", "kernels_f32.cu", "kernels_f64.cu", "kernels_f16.cu", "kernels.h"):
-        with open(os.path.join(ROOT, "paper_1508_07982_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1508_07982_gb300", "csrc", name)) as fh:
+                text = fh.read()
+        else:
+            text = read(name)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

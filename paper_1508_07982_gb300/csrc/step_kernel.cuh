@@ -330,11 +330,13 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
 
 // One sub-step of one level (Alg. 2 StreamCollide generalised to every level): pull stream with
 // boundary treatment and coalescence, then collide owned cells; ghost layers 1-2 are streamed
-// only, and only the values a later pull reads.  Owned cells: each thread walks 2^lzc cells of
+// only, and only the values a later pull reads.  The grid: first the coupled cells' CTAs (owned
+// cells with a coalescence link, one thread per cell), then the column walk over the other owned
+// cells, then the ghost work list of this sub-step.  In the walk each thread walks 2^lzc cells of
 // one (x, y) column of a brick; the source offsets of a cell inside the brick are computed once
-// per column, obstacle cells are skipped by a per-column bitmap, and a per-cell link mask (read
-// where the brick needs it) routes the few links that are not plain loads to pull_general.  CTAs
-// after the owned part cover the ghost work list of this sub-step.
+// per column, obstacle and coupled cells are skipped by a per-column bitmap, and a per-cell link
+// mask (read where the brick needs it) routes the few links that are not plain loads to
+// pull_general.
 // FP32 storage stages each cell's 19 pulls in shared memory with cp.async, two cells deep; the
 // other storage types load into registers.  The same array receives general-pull values.
 template <typename T, typename C>
@@ -463,6 +465,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int64_t bid, StepS
             }
             return sidx;
         };
+        // cells the walk skips: obstacle cells, and coupled cells (their own CTAs)
         const uint32_t solid = need_mask ? __ldg(a.lv.colsolid + (brick << B2s) + col) : 0u;
         const LevelParams* P = a.params;
         const C le = Par<C>::le(P), lo = Par<C>::lo(P);
