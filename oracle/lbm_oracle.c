@@ -20,7 +20,7 @@
  *   [coalesce(L) if L<finest]; return if L==0;
  *   collide(L); [step(L+1)]; boundary(L); stream(L); [coalesce(L) if L<finest]
  *
- * Readings of passages the paper leaves open (each also listed in the design doc):
+ * Readings of passages the paper leaves open:
  *  - moments (Eq. fvelocity) are taken of f, not f^eq (the printed f^eq is a typo);
  *  - D3Q19 weights 1/3, 1/18, 1/36 (standard; not printed);
  *  - velocity bounce-back adds 6 w_a rho0 (e_a . u_w) (named only, Sec. 5.2);
