@@ -47,6 +47,8 @@ def test_invalid_descriptions_are_rejected_on_the_host(lbm):
         dict(inputs.cavity_case(), lmax=9),
         dict(inputs.cavity_case(), bc=["periodic", "noslip", "noslip", "noslip", "noslip", "noslip"]),
         dict(inputs.cavity_case(), rho0=0.0),
+        dict(inputs.cavity_case(), u_shift=(0.25, 0.2, 0.0)),       # |u_shift| >= 0.3
+        dict(inputs.cavity_case(), u_shift=(float("nan"), 0.0, 0.0)),
     ]
     for case in bad:
         with pytest.raises(lbm.LBMError) as ei:
