@@ -204,6 +204,21 @@ def _roofline(f, lev, precision, peaks, peak_kind):
             "per_level": per_level}
 
 
+# FP64 arithmetic of the FP64 step kernel: 220 FP64 thread instructions per cell update (ncu,
+# profiles/step_kernel_sphere_channel_fp64.md).  Peak: 2 per clock per SM (the nominal 1.25 TFLOP/s
+# FP64 of GB300 as FMAs over 152 SMs at 2.07 GHz).
+FP64_INST_PER_UPDATE = 220
+FP64_INST_PEAK_G = 2 * 152 * 2.07
+
+
+def _fp64_alu_roofline(r):
+    """The FP64 kernel against its arithmetic bound, from the same launch timing as r."""
+    ach = r["achieved"] / (2 * 19 * 8) * FP64_INST_PER_UPDATE      # GB/s -> G updates/s -> G inst/s
+    return {"bound": "alu", "achieved": round(ach, 1), "peak": FP64_INST_PEAK_G, "unit": "G FP64 inst/s",
+            "frac": round(ach / FP64_INST_PEAK_G, 4),
+            "peak_source": "derived: 2 FP64 thread instructions per clock per SM x 152 SMs x 2.07 GHz"}
+
+
 _COUNTS = {}
 
 
@@ -519,6 +534,7 @@ def main():
             r = _roofline(g, lev_v, prec, peaks, peak_kind)
             entry["roofline"] = {kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
             if prec == "fp64":
+                entry["roofline_alu"] = _fp64_alu_roofline(r)
                 ref64 = g
             else:
                 entry["error_vs_fp64_after_%d_steps" % (k + 3)] = _precision_error(g, ref64)
