@@ -147,6 +147,20 @@ def _ncu_traffic(precision):
     return e.get("dram_bytes_per_launch")
 
 
+def _max_over_ranks(ms, dist, device):
+    """The slowest rank's time of the timed region (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(world, updates_per_step, steps, ms):
+    """Whole-job GLUPS: every rank runs its own replica of the workload (weak scaling), so the job
+    updates world x updates_per_step cells per coarse step in the slowest rank's time ms."""
+    return world * updates_per_step * steps / (ms / 1e3) / 1e9
+
+
 def _timed_graph(f, torch, steps):
     """K coarse steps of graph replay on the current stream, timed with CUDA events."""
     stream = torch.cuda.current_stream()
@@ -513,11 +527,9 @@ def main():
     f.step_coarse(max(args.warmup, 3))
     ms_k, lev = _timed_kernels(f, torch, args.steps)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = _max_over_ranks(ms, dist, "cuda")
     upd = f.cell_updates_per_coarse_step()
-    value = world * upd * args.steps / (ms / 1e3) / 1e9
+    value = _job_value(world, upd, args.steps, ms)
     roof = _roofline(f, lev, args.precision, peaks, peak_kind)
     roof["kernel_timing_pass_ms_per_step"] = round(ms_k / args.steps, 5)
     cfg = _config(case, f)
