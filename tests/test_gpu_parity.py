@@ -74,6 +74,18 @@ def test_cavity_fp64_matches_the_oracle_after_100_coarse_steps(lbm, oracle_mod):
     assert _compare(f, o) < TOL64
 
 
+@pytest.mark.parametrize("cfg", [(0, 2), (1, 4), (3, 3)])
+def test_cavity_matches_the_oracle_in_every_launch_configuration(lbm, oracle_mod, cfg):
+    """The cavity (coupled cells along the whole level-0/1 interface, which run in their own CTAs
+    at the head of each launch) in other launch configurations: cells per thread 1, 2, 8 and 2-4
+    CTAs per SM; 30 coarse steps."""
+    f, o = _pair(lbm, oracle_mod, inputs.cavity_case())
+    f.set_kernel_config(*cfg)
+    f.step_coarse(30)
+    o.step(30)
+    assert _compare(f, o) < TOL64
+
+
 def test_uniform_periodic_fp64_matches_the_oracle(lbm, oracle_mod):
     """Uniform periodic 64^3, SRT omega = 1.9, Taylor-Green modes + density noise, 200 steps."""
     case = inputs.periodic_case(n=64, B=16, collision="srt", omega=1.9)
