@@ -48,6 +48,7 @@ def _args():
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-forest leg")
     p.add_argument("--no-net", action="store_true", help="skip the warm-start net leg")
     p.add_argument("--no-lid", action="store_true", help="skip the paper's lid-driven benchmark leg")
+    p.add_argument("--no-uniform", action="store_true", help="skip the uniform 512^3 stream-collide leg")
     return p.parse_args()
 
 
@@ -401,6 +402,29 @@ def _lid(lbm, torch, peaks, peak_kind, steps=100, steps64=20):
     return out
 
 
+def _uniform(lbm, torch, peaks, peak_kind, n=512, steps=100):
+    """The pure stream-collide case: a uniform periodic n^3 grid (one level, 32^3 blocks), SRT
+    omega = 1.9, FP32S, started from the uniform flow (0.02, 0, 0).  No interfaces and no walls:
+    the column walk alone, the kernel's ceiling on the refined workloads."""
+    from paper_1508_07982_gb300 import inputs
+    case = inputs.periodic_case(n=n, B=32, collision="srt", omega=1.9)
+    f = lbm.Forest(case, precision="fp32s")
+    f.init_uniform((0.02, 0.0, 0.0))
+    f.step_coarse(3)
+    torch.cuda.synchronize()
+    ms = _timed_graph(f, torch, steps)
+    _, lev = _timed_kernels(f, torch, steps)
+    upd = f.cell_updates_per_coarse_step()
+    r = _roofline(f, lev, "fp32s", peaks, peak_kind)
+    out = {"workload": "uniform periodic %d^3 (one level, 32^3 blocks), SRT omega 1.9, FP32S, uniform start (0.02, 0, 0)" % n,
+           "value": round(upd * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms / steps, 5),
+           "steps": steps,
+           "roofline": dict({kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac")}, traffic=None,
+                            kernel="step_kernel level 0 (the only level)")}
+    f.close()
+    return out
+
+
 def _fluid_counts_case(case):
     from paper_1508_07982_gb300 import lbm
     p = lbm.Plan(case)
@@ -559,6 +583,7 @@ def main():
     batch = _batch(lbm, torch) if rank == 0 and not args.no_batch else None
     net = _net(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_net else None
     lid = _lid(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_lid else None
+    uni = _uniform(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_uniform else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(case)
@@ -576,6 +601,8 @@ def main():
         line["warm_start_net"] = net
     if lid:
         line["paper_lid_benchmark"] = lid
+    if uni:
+        line["uniform_512"] = uni
     if rank == 0:
         print(json.dumps(line), flush=True)
     f.close()
