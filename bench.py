@@ -402,7 +402,7 @@ def _lid(lbm, torch, peaks, peak_kind, steps=100, steps64=20):
     return out
 
 
-def _uniform(lbm, torch, peaks, peak_kind, n=512, steps=100):
+def _uniform_grid_leg(lbm, torch, peaks, peak_kind, n=512, steps=100):
     """The pure stream-collide case: a uniform periodic n^3 grid (one level, 32^3 blocks), SRT
     omega = 1.9, FP32S, started from the uniform flow (0.02, 0, 0).  No interfaces and no walls:
     the column walk alone, the kernel's ceiling on the refined workloads."""
@@ -583,7 +583,7 @@ def main():
     batch = _batch(lbm, torch) if rank == 0 and not args.no_batch else None
     net = _net(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_net else None
     lid = _lid(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_lid else None
-    uni = _uniform(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_uniform else None
+    uni = _uniform_grid_leg(lbm, torch, peaks, peak_kind) if rank == 0 and not args.no_uniform else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline(case)
