@@ -54,6 +54,9 @@
 #define ORC_MAXSPH 64
 #define ORC_MAXREG 64
 #define PAD 5
+/* Loops over fewer items run on one thread: for the small pinned cases the cost of waking the
+ * OpenMP team exceeds the work.  Every loop is element-wise, so the result does not depend on it. */
+#define ORC_PAR_MIN 16384
 
 enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_VELOCITY = 2, BC_FREESLIP = 3 };
 enum { COLL_SRT = 0, COLL_TRT = 1 };
@@ -590,7 +593,7 @@ static int build_lists(orc *o, int L) {
 
 static void op_collide(orc *o, int L) {
     olevel *V = &o->lv[L];
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if (V->nC > ORC_PAR_MIN)
     for (long i = 0; i < V->nC; i++)
         collide_cell(V->f + V->C[i] * Q, o->d.collision, o->le[L], o->lo[L], o->acc[L], o->d.rho0);
 }
@@ -598,7 +601,7 @@ static void op_collide(orc *o, int L) {
 /* Eq. (ctof): every fine ghost cell of layers 1-4 receives all 19 PDFs of its coarse parent. */
 static void op_explode(orc *o, int L) {
     olevel *V = &o->lv[L], *P = &o->lv[L - 1];
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if (V->nG > ORC_PAR_MIN)
     for (long i = 0; i < V->nG; i++)
         memcpy(V->f + V->G[i] * Q, P->f + V->Gp[i] * Q, Q * sizeof(double));
 }
@@ -607,7 +610,7 @@ static void op_explode(orc *o, int L) {
  * for every direction a whose target b + e_a streams, the bounced PDF of that target. */
 static void op_boundary(orc *o, int L) {
     olevel *V = &o->lv[L];
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if (V->nBd > ORC_PAR_MIN)
     for (long i = 0; i < V->nBd; i++) {
         long b = V->Bd[i];
         int x, y, z;
@@ -644,7 +647,7 @@ static void op_boundary(orc *o, int L) {
 static void op_stream(orc *o, int L) {
     olevel *V = &o->lv[L];
     memcpy(V->tmp, V->f, V->ncell * Q * sizeof(double));
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if (V->nS > ORC_PAR_MIN)
     for (long i = 0; i < V->nS; i++) {
         long c = V->S[i];
         int x, y, z;
@@ -661,7 +664,7 @@ static void op_stream(orc *o, int L) {
  * block from the finer level; the fine values are those after both fine sub-steps. */
 static void op_coalesce(orc *o, int L) {
     olevel *V = &o->lv[L], *Fv = &o->lv[L + 1];
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if (V->nK > ORC_PAR_MIN)
     for (long k = 0; k < V->nK; k++) {
         int a = V->Ka[k];
         const long *ch = V->Kch + 8 * k;
