@@ -273,6 +273,22 @@ def plane_poiseuille_case(B=4, ny_roots=4, nxz_roots=1, where="bottom", lambda_e
                 lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(accel, 0.0, 0.0))
 
 
+def plane_couette_case(B=4, nz_roots=4, nxy_roots=1, where=None, lambda_e0=0.5, u_wall=(0.05, 0.0, 0.0)):
+    """Plane Couette flow: a velocity wall at z = H moving tangentially with u_wall, a no-slip wall
+    at z = 0, periodic x and y, no force.  `where` refines the cells next to the moving wall
+    ("top"), the fixed wall ("bottom"), both, or nothing (None)."""
+    H = nz_roots * B
+    regs = []
+    if where in ("bottom", "both"):
+        regs.append(("box", 1, (0, 0, 0), (1e9, 1e9, 0.5)))
+    if where in ("top", "both"):
+        regs.append(("box", 1, (0, 0, H - 0.5), (1e9, 1e9, H)))
+    return dict(root=(nxy_roots, nxy_roots, nz_roots), B=B, lmax=1 if regs else 0, collision="trt", rho0=1.0,
+                bc=["periodic"] * 4 + ["noslip", "velocity"],
+                bc_u=[(0.0, 0.0, 0.0)] * 5 + [tuple(float(v) for v in u_wall)], spheres=[], regions=regs,
+                lambda_e0=lambda_e0, magic=3.0 / 16.0, accel=(0.0, 0.0, 0.0))
+
+
 # --------------------------------------------------------------------------- fields
 
 def _splitmix64(x):

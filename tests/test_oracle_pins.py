@@ -588,3 +588,77 @@ def test_shear_mode_between_free_slip_walls_decays_at_the_viscous_rate(oracle_mo
     nu = (1 / le - 0.5) / 3
     rate = -math.log(a2 / a1) / 200
     assert abs(rate / (nu * (math.pi / H) ** 2) - 1) < 5e-3
+
+
+# --------------------------------------------------------------------------- velocity walls
+
+def test_velocity_wall_injects_the_closed_form_momentum(oracle_mod):
+    """Velocity bounce-back (Sec. 5.2; read as f_a = f~_abar + 6 w_a rho0 e_a . u_w): from rest,
+    one step adds, per wall cell, no mass and the momentum 6 rho0 sum_{a: e_az = -1} w_a e_a (e_a . u_w)
+    = rho0 u_w / 3 (two edge directions of weight 1/36 per tangential axis), whatever the rates.
+    A wrong coefficient, sign or component of the wall term changes these totals."""
+    uw = (0.05, -0.02, 0.0)
+    case = inputs.plane_couette_case(nxy_roots=2, u_wall=uw, lambda_e0=1.3)
+    o = oracle_mod.Oracle(case)
+    o.init_fields(inputs.uniform_field())
+    m0 = o.mass_momentum()
+    o.step(1)
+    m1 = o.mass_momentum()
+    n_wall = (2 * 4) ** 2
+    assert abs(m1[0] - m0[0]) < 1e-12
+    assert abs(m1[1] - n_wall * uw[0] / 3) < 1e-14
+    assert abs(m1[2] - n_wall * uw[1] / 3) < 1e-14
+    assert abs(m1[3]) < 1e-14
+
+
+@pytest.mark.parametrize("where", [None, "top", "bottom", "both"])
+def test_plane_couette_profile_is_exact(oracle_mod, where):
+    """Plane Couette flow between a no-slip wall (z = 0) and a moving velocity wall (z = H), TRT with
+    Lambda = 3/16: the steady profile u = u_w z / H, with the walls halfway between the boundary
+    cells and the first fluid cells (Sec. 2.2), is reproduced to round-off on a uniform grid and
+    with refinement at either wall (a linear profile has no second derivative for the
+    interface treatment to miss)."""
+    le0, uw = 0.5, (0.05, -0.02, 0.0)
+    case = inputs.plane_couette_case(where=where, lambda_e0=le0, u_wall=uw)
+    o = oracle_mod.Oracle(case)
+    assert o.nlev == (1 if where is None else 2)
+    o.init_fields(inputs.uniform_field())
+    o.step(2000)
+    H = 16
+    err = 0.0
+    for L in range(o.nlev):
+        X, Y, Z = o.coords(L)
+        rho, u = o.macro(L)
+        cls, flg = o.classes(L)
+        own = (cls == 1) & (flg == 0)
+        assert own.any()
+        z = (Z + 0.5) * 2.0 ** -L
+        for k in range(3):
+            err = max(err, np.abs(u[k] - uw[k] * z / H)[own].max() / uw[0])
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("where", [None, "top"])
+def test_plane_couette_wall_stress_matches_the_closed_form(oracle_mod, where):
+    """At steady state the momentum the moving wall passes to the fluid per step equals the viscous
+    shear stress rho0 nu u_w / H per unit wall area, nu = (1/lambda_e - 1/2)/3 (Sec. 2).  The
+    exchange is summed over the wall links of the top fluid layer from its post-collision state:
+    each link takes f~_abar (direction abar towards the wall) and returns f~_abar + 6 w rho0 e_a . u_w."""
+    e, w, opp = oracle_mod.lattice()
+    le0, U = 0.5, 0.05
+    case = inputs.plane_couette_case(where=where, lambda_e0=le0, u_wall=(U, 0.0, 0.0))
+    o = oracle_mod.Oracle(case)
+    o.init_fields(inputs.uniform_field())
+    o.step(2000)
+    L = o.nlev - 1
+    N = 16 << L
+    X, Y, Z = o.coords(L)
+    cls, flg = o.classes(L)
+    top = (cls == 1) & (flg == 0) & (Z == N - 1)
+    ft = o.get_f(L, post_collision=True)[top]
+    dP = 0.0
+    for a in range(19):
+        if e[a][2] == -1:
+            dP += e[a][0] * (2.0 * ft[:, opp[a]] + 6.0 * w[a] * e[a][0] * U).sum()
+    nu_L = (1.0 / o.params()[0][L] - 0.5) / 3.0      # level-L lattice units
+    assert abs(dP / top.sum() / (nu_L * U / N) - 1.0) < 1e-10
