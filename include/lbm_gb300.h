@@ -183,7 +183,10 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps);
 
 /* Macroscopic fields (Eq. fvelocity; the velocity adds a_L/2 as in Sec. 2.1) of the current
  * state of one level, block-major FP64: rho[n_cells], u[3][n_cells]; NaN on obstacle cells.
- * Either output may be NULL.  Synchronises the stream when on_device = 0. */
+ * level = -1 returns every level in one array, level 0 first, each level block-major:
+ * rho[N], u[3][N] with N the sum of the levels' n_cells (lbm_get_block_table gives each level's
+ * blocks in the same order).  Either output may be NULL.  Synchronises the stream when
+ * on_device = 0. */
 lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double* u,
                                int32_t on_device);
 
@@ -352,16 +355,25 @@ lbm_status lbm_net_set_backend(lbm_net* n, int32_t backend);
  * where cudaMalloc is not allowed; runtimes that own all device memory through their own pool;
  * hosts that forbid dynamic allocation after start-up).  It calls no cudaMalloc, cudaFree or
  * other allocating routine.  Its per-CTA partial sums live in one fixed device array of
- * (LBM_NOALLOC_MAX_CELLS / LBM_NOALLOC_CELLS_PER_CTA) x 4 doubles = 512 KiB, which every GPU that
+ * (LBM_NOALLOC_MAX_CELLS / LBM_NOALLOC_CELLS_PER_CTA) x 5 doubles = 640 KiB, which every GPU that
  * loads the library holds until the process exits.
  *
- *   pdfs      device pointer, [19][n_cells] in the storage layout of `precision` (LBM_FP64: f;
- *             LBM_FP32S / LBM_FP16S: f - w rho0), e.g. the output of lbm_get_pdfs
+ *   pdfs      device pointer, [19][n_cells] in the storage layout of `precision`: LBM_FP64 holds f
+ *             (for example the output of lbm_get_pdfs, which is always FP64 f); LBM_FP32S and
+ *             LBM_FP16S hold f - f^eq(rho0, u_shift), the forests' own storage of those precisions
  *   n_cells   0 .. LBM_NOALLOC_MAX_CELLS; larger counts return LBM_EINVAL without launching
- *   rho0      reference density (adds back the shift of the shifted layouts)
- *   out       device pointer to 4 doubles: {sum rho, sum j_x, sum j_y, sum j_z} with
- *             j = sum_a e_a f_a; cells whose 19 values are not all finite (obstacles) are skipped
+ *   rho0      reference density; with the shifted layouts each finite cell adds rho0 to rho
+ *   u_shift   host pointer to 3 doubles, the storage shift of the shifted layouts (NULL = 0); each
+ *             finite cell adds rho0 u_shift to j.  Ignored for LBM_FP64
+ *   out       device pointer to 5 doubles: {sum rho, sum j_x, sum j_y, sum j_z, skipped}, with
+ *             j = sum_a e_a f_a of the values given.  Cells whose 19 values do not sum to a finite
+ *             number are left out and counted in `skipped`: obstacle cells (NaN by design) and any
+ *             diverged fluid cell, so a count above the caller's obstacle count flags divergence
  *   stream    cudaStream_t; the call is asynchronous
+ * Body force: a forest's stored state is post-collision, whose momentum includes rho0 a per fluid
+ * cell (Sec. 2.1).  lbm_reduce_mass_momentum subtracts it; this entry point returns j of the values
+ * as given, so callers with a body force subtract rho0 a per fluid cell themselves.
+ * A CUDA error already pending when the call starts is returned as LBM_ECUDA without launching.
  * The first call on each device looks up the device address of the fixed array
  * (cudaGetSymbolAddress); make that first call before capturing any stream on that device.
  * All calls share the array and it keeps the last call's partial sums; every call writes each
@@ -370,7 +382,7 @@ lbm_status lbm_net_set_backend(lbm_net* n, int32_t backend);
 #define LBM_NOALLOC_CELLS_PER_CTA 4096
 #define LBM_NOALLOC_MAX_CELLS (16384 * 4096)
 lbm_status lbm_mass_momentum_noalloc(const void* pdfs, int32_t precision, int64_t n_cells, double rho0,
-                                     double* out, void* stream);
+                                     const double* u_shift, double* out, void* stream);
 
 #ifdef __cplusplus
 }

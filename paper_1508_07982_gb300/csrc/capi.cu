@@ -699,10 +699,14 @@ lbm_status lbm_step_coarse(lbm_forest* f, int32_t n_steps) {
 }
 
 lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double* u, int32_t on_device) {
-    lbm_status s = check_level(f, level);
-    if (s) return s;
+    if (!f) return fail(LBM_EINVAL, "forest is NULL");
+    lbm_status s = LBM_OK;
     const Plan& P = f->plan;
-    const int64_t n = owned_cells(f, level);
+    // level -1: every level, level after level, in one array (u components N_all apart)
+    const int L0 = level < 0 ? 0 : level, L1 = level < 0 ? P.nlev - 1 : level;
+    if (level != -1 && (s = check_level(f, level))) return s;
+    int64_t n = 0;
+    for (int L = L0; L <= L1; L++) n += owned_cells(f, L);
     if (n == 0) return LBM_OK;
     double *dr = rho, *du = u;
     if (!on_device) {
@@ -711,7 +715,12 @@ lbm_status lbm_get_macroscopic(lbm_forest* f, int32_t level, double* rho, double
         dr = rho ? st : nullptr;
         du = u ? st + n : nullptr;
     }
-    f->L->macro(f->dl[level], f->cur[level], P.LB, f->d_params + level, P.d.rho0, dr, du, f->stream);
+    int64_t off = 0;
+    for (int L = L0; L <= L1; L++) {
+        f->L->macro(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, dr ? dr + off : nullptr,
+                    du ? du + off : nullptr, n, f->stream);
+        off += owned_cells(f, L);
+    }
     CU(cudaGetLastError());
     if (!on_device) {
         if (rho) CU(cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
@@ -810,7 +819,7 @@ lbm_status lbm_velocity_residual(lbm_forest* f, double* r) {
         if (s) return s;
         double* st = static_cast<double*>(f->d_stage);
         if (!f->uprev[L]) CU(cudaMalloc(&f->uprev[L], size_t(n) * 3 * sizeof(double)));
-        f->L->macro(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, st, st + n, f->stream);
+        f->L->macro(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, st, st + n, n, f->stream);
         residual_kernel<<<G, 256, 0, f->stream>>>(st + n, f->uprev[L], f->dl[L].cell, n, std::ldexp(1.0, -3 * L), part);
     }
     reduce_final_kernel<<<1, 256, 0, f->stream>>>(f->d_rpart, P.nlev * G, f->d_out);

@@ -75,7 +75,7 @@ struct Launchers {
     void (*init)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, const double* rho,
                  const double* u, int uniform, const double u_const[4], int collision, cudaStream_t s);
     void (*macro)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double* rho, double* u,
-                  cudaStream_t s);
+                  int64_t ustride, cudaStream_t s);
     void (*get_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, double* out, cudaStream_t s);
     void (*set_pdfs)(const DevLevel& lv, int cur, int LB, double rho0, const double* in, cudaStream_t s);
     void (*reduce)(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double w, double* partial,

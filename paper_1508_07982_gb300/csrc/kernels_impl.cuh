@@ -33,10 +33,10 @@ struct LaunchImpl {
             init_kernel<T, C, LBM_SRT><<<grid, 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u, uniform, uc[0], uc[1], uc[2], uc[3]);
     }
     static void macro(const DevLevel& lv, int cur, int LB, const LevelParams* P, double rho0, double* rho, double* u,
-                      cudaStream_t s) {
+                      int64_t ustride, cudaStream_t s) {
         const int64_t n = int64_t(lv.nown) << (3 * LB);
         if (n == 0) return;
-        macro_kernel<T><<<int((n + 255) / 256), 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u);
+        macro_kernel<T><<<int((n + 255) / 256), 256, 0, s>>>(lv, cur, LB, P, rho0, rho, u, ustride);
     }
     static void get_pdfs(const DevLevel& lv, int cur, int LB, double rho0, double* out, cudaStream_t s) {
         const int64_t n = int64_t(lv.nown) << (3 * LB);

@@ -22,9 +22,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxCtas = LBM_NOALLOC_MAX_CELLS / LBM_NOALLOC_CELLS_PER_CTA;
 
-// Partial sums {rho, jx, jy, jz} of each CTA.  Every GPU that loads the library holds this
-// array (kMaxCtas * 4 doubles) until the process exits.  All calls share it.
-static __device__ __align__(256) double g_partial[kMaxCtas * 4];
+// Partial sums {rho, jx, jy, jz, skipped cells} of each CTA.  Every GPU that loads the library
+// holds this array (kMaxCtas * 5 doubles) until the process exits.  All calls share it.
+static __device__ __align__(256) double g_partial[kMaxCtas * 5];
 
 
 __host__ __device__ constexpr int ex(int q) {
@@ -40,12 +40,16 @@ __host__ __device__ constexpr int ez(int q) {
 template <typename T> __device__ __forceinline__ double as_double(T v) { return double(v); }
 template <> __device__ __forceinline__ double as_double<__half>(__half v) { return double(__half2float(v)); }
 
-// One CTA per LBM_NOALLOC_CELLS_PER_CTA cells; non-finite cells (obstacles hold NaN) are skipped.
+// One CTA per LBM_NOALLOC_CELLS_PER_CTA cells.  Cells whose 19 values do not sum to a finite number
+// (obstacle cells hold NaN by design; a diverged fluid cell would too) are left out of the sums and
+// counted in the fifth slot.  The shifted layouts hold f - f^eq(rho0, u0), whose moments are rho - rho0
+// and j - rho0 u0: each finite cell adds rho0 and rho0 u0 back.
 template <typename T, bool SHIFTED>
-__global__ void __launch_bounds__(kThreads) partial_kernel(const T* f, long long n, double rho0, double* partial) {
+__global__ void __launch_bounds__(kThreads) partial_kernel(const T* f, long long n, double rho0, double u0x,
+                                                           double u0y, double u0z, double* partial) {
     const long long begin = (long long)blockIdx.x * LBM_NOALLOC_CELLS_PER_CTA;
     const long long end = begin + LBM_NOALLOC_CELLS_PER_CTA < n ? begin + LBM_NOALLOC_CELLS_PER_CTA : n;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long i = begin + threadIdx.x; i < end; i += kThreads) {
         double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
@@ -56,41 +60,44 @@ __global__ void __launch_bounds__(kThreads) partial_kernel(const T* f, long long
             jy += ey(q) * v;
             jz += ez(q) * v;
         }
-        if (!isfinite(r)) continue;
+        if (!isfinite(r)) {
+            s[4] += 1.0;
+            continue;
+        }
         s[0] += SHIFTED ? rho0 + r : r;
-        s[1] += jx;
-        s[2] += jy;
-        s[3] += jz;
+        s[1] += SHIFTED ? jx + rho0 * u0x : jx;
+        s[2] += SHIFTED ? jy + rho0 * u0y : jy;
+        s[3] += SHIFTED ? jz + rho0 * u0z : jz;
     }
-    __shared__ double red[4][kThreads / 32];
+    __shared__ double red[5][kThreads / 32];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < 5; k++) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 5) {
         double v = 0.0;
         for (int w = 0; w < kThreads / 32; w++) v += red[threadIdx.x][w];
-        partial[blockIdx.x * 4 + threadIdx.x] = v;
+        partial[blockIdx.x * 5 + threadIdx.x] = v;
     }
 }
 
 // Sums the partials of the CTAs that the call launched, in a fixed order.
 __global__ void __launch_bounds__(kThreads) final_kernel(const double* partial, int nctas, double* out) {
-    __shared__ double red[4][kThreads];
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    __shared__ double red[5][kThreads];
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nctas; i += kThreads)
-        for (int k = 0; k < 4; k++) s[k] += partial[4 * i + k];
-    for (int k = 0; k < 4; k++) red[k][threadIdx.x] = s[k];
+        for (int k = 0; k < 5; k++) s[k] += partial[5 * i + k];
+    for (int k = 0; k < 5; k++) red[k][threadIdx.x] = s[k];
     __syncthreads();
     for (int w = kThreads / 2; w > 0; w >>= 1) {
         if (int(threadIdx.x) < w)
-            for (int k = 0; k < 4; k++) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+            for (int k = 0; k < 5; k++) red[k][threadIdx.x] += red[k][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < 5) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 // Device address of g_partial, looked up once per device (the host-side symbol is only a
@@ -107,7 +114,7 @@ lbm_status fail(lbm_status s, const char* msg) {
 }  // namespace
 
 extern "C" lbm_status lbm_mass_momentum_noalloc(const void* pdfs, int32_t precision, int64_t n_cells, double rho0,
-                                                double* out, void* stream) {
+                                                const double* u_shift, double* out, void* stream) {
     if (!pdfs || !out) return fail(LBM_EINVAL, "pdfs and out must be device pointers");
     if (precision < LBM_FP64 || precision > LBM_FP16S) return fail(LBM_EINVAL, "unknown precision");
     if (n_cells < 0) return fail(LBM_EINVAL, "negative cell count");
@@ -117,6 +124,7 @@ extern "C" lbm_status lbm_mass_momentum_noalloc(const void* pdfs, int32_t precis
                  (long long)n_cells, LBM_NOALLOC_MAX_CELLS);
         return fail(LBM_EINVAL, buf);
     }
+    const double u0[3] = {u_shift ? u_shift[0] : 0.0, u_shift ? u_shift[1] : 0.0, u_shift ? u_shift[2] : 0.0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(LBM_ECUDA, "no usable CUDA device");
     double* partial;
@@ -130,17 +138,30 @@ extern "C" lbm_status lbm_mass_momentum_noalloc(const void* pdfs, int32_t precis
         }
         partial = g_addr[dev];
     }
+    // an error left pending by earlier work is reported as such, not as this call's launch failure
+    const cudaError_t prior = cudaPeekAtLastError();
+    if (prior != cudaSuccess) {
+        std::string m = std::string("a CUDA error from earlier work is pending: ") + cudaGetErrorString(prior);
+        return fail(LBM_ECUDA, m.c_str());
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nctas = int((n_cells + LBM_NOALLOC_CELLS_PER_CTA - 1) / LBM_NOALLOC_CELLS_PER_CTA);
     if (nctas > 0) {
         if (precision == LBM_FP64)
-            partial_kernel<double, false><<<nctas, kThreads, 0, s>>>(static_cast<const double*>(pdfs), n_cells, rho0, partial);
+            partial_kernel<double, false><<<nctas, kThreads, 0, s>>>(static_cast<const double*>(pdfs), n_cells, rho0,
+                                                                      u0[0], u0[1], u0[2], partial);
         else if (precision == LBM_FP32S)
-            partial_kernel<float, true><<<nctas, kThreads, 0, s>>>(static_cast<const float*>(pdfs), n_cells, rho0, partial);
+            partial_kernel<float, true><<<nctas, kThreads, 0, s>>>(static_cast<const float*>(pdfs), n_cells, rho0,
+                                                                    u0[0], u0[1], u0[2], partial);
         else
-            partial_kernel<__half, true><<<nctas, kThreads, 0, s>>>(static_cast<const __half*>(pdfs), n_cells, rho0, partial);
+            partial_kernel<__half, true><<<nctas, kThreads, 0, s>>>(static_cast<const __half*>(pdfs), n_cells, rho0,
+                                                                     u0[0], u0[1], u0[2], partial);
     }
     final_kernel<<<1, kThreads, 0, s>>>(partial, nctas, out);
-    if (cudaGetLastError() != cudaSuccess) return fail(LBM_ECUDA, "kernel launch failed");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        std::string m = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+        return fail(LBM_ECUDA, m.c_str());
+    }
     return LBM_OK;
 }

@@ -75,20 +75,41 @@ __device__ __forceinline__ double shift_value(int q, double rho0, const double (
 }
 
 // ------------------------------------------------------------------ shared-memory staging
-// 4-byte asynchronous copies global -> shared (LDGSTS); a false predicate zero-fills without
-// reading global memory.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(pred ? 4 : 0) : "memory");
+// Bulk asynchronous copies global -> shared on the TMA engine (the non-tensor form: 16-byte aligned
+// addresses, sizes a multiple of 16 bytes), completing on an mbarrier by transaction count.
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sh_addr(bar)) : "memory");
+}
+// One arrival that also raises the phase's expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sh_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sh_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(sh_addr(bar))
+                 : "memory");
+}
+// Orders this thread's generic-proxy shared-memory accesses before later bulk copies into the
+// same bytes.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// Cells whose pulls are in flight per thread in the FP32 column walk (pipeline depth).
-#ifndef LBM_CP_STAGES
-#define LBM_CP_STAGES 2
-#endif
+// Iterations of a bounded mbarrier wait (each try_wait itself blocks for a while): far beyond any
+// copy's completion time; running out marks the launch's error flag.
+constexpr int kWaitIters = 1 << 22;
 
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
 // v holds f (or its shifted form) on entry and f-tilde on exit.  R is rho (or rho - rho0).
@@ -748,16 +769,17 @@ __global__ void init_kernel(const DevLevel lv, int cur, int LB, const LevelParam
 }
 
 // rho and u (+ a/2) of owned cells from the stored post-collision state: collision keeps rho and
-// adds rho0 a to the momentum, so u_out = j~/rho0 - a/2 (Sec. 2.1).
+// adds rho0 a to the momentum, so u_out = j~/rho0 - a/2 (Sec. 2.1).  u holds the three components
+// `us` values apart (the level's cell count, or the total over all levels for the all-level layout).
 template <typename T>
 __global__ void macro_kernel(const DevLevel lv, int cur, int LB, const LevelParams* P, double rho0, double* rho,
-                             double* u) {
+                             double* u, int64_t us) {
     const int64_t nown_cells = int64_t(lv.nown) << (3 * LB);
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nown_cells) return;
     if (lv.cell[i] != CK_FLUID) {
         if (rho) rho[i] = __longlong_as_double(0x7ff8000000000000ULL);
-        if (u) u[i] = u[nown_cells + i] = u[2 * nown_cells + i] = __longlong_as_double(0x7ff8000000000000ULL);
+        if (u) u[i] = u[us + i] = u[2 * us + i] = __longlong_as_double(0x7ff8000000000000ULL);
         return;
     }
     const T* f = static_cast<const T*>(lv.f[cur]);
@@ -773,8 +795,8 @@ __global__ void macro_kernel(const DevLevel lv, int cur, int LB, const LevelPara
     if (rho) rho[i] = Store<T>::shifted ? rho0 + R : R;
     if (u) {   // the shifted layouts hold j - rho0 u0
         u[i] = jx / rho0 + lv.u0[0] - 0.5 * P->acc[0];
-        u[nown_cells + i] = jy / rho0 + lv.u0[1] - 0.5 * P->acc[1];
-        u[2 * nown_cells + i] = jz / rho0 + lv.u0[2] - 0.5 * P->acc[2];
+        u[us + i] = jy / rho0 + lv.u0[1] - 0.5 * P->acc[1];
+        u[2 * us + i] = jz / rho0 + lv.u0[2] - 0.5 * P->acc[2];
     }
 }
 

@@ -107,7 +107,7 @@ def library():
             "lbm_launches_per_coarse_step": [P, i32p],
             "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_get_kernel_config": [P, i32p, i32p],
-            "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, P, P],
+            "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, dp, P, P],
             "lbm_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
             "lbm_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P)],
             "lbm_batch_step": [P, ctypes.c_int32],
@@ -214,16 +214,19 @@ def make_desc(case, precision="fp64"):
     return d
 
 
-def lbm_mass_momentum_noalloc(pdfs, precision, n_cells, rho0, out, stream=None):
+def lbm_mass_momentum_noalloc(pdfs, precision, n_cells, rho0, out, stream=None, u_shift=None):
     """Totals of a device PDF array without any allocation (see include/lbm_gb300.h).  pdfs and
-    out are device tensors (or raw device addresses); out receives 4 doubles."""
+    out are device tensors (or raw device addresses); out receives 5 doubles {rho, jx, jy, jz,
+    skipped cells}.  u_shift: the storage shift of the shifted layouts (None = 0)."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     p = pdfs if isinstance(pdfs, int) else pdfs.data_ptr()
     o = out if isinstance(out, int) else out.data_ptr()
+    us = None if u_shift is None else np.ascontiguousarray(u_shift, dtype=np.float64)
     _check(library().lbm_mass_momentum_noalloc(ctypes.c_void_p(p), PRECISION[precision], n_cells, rho0,
-                                                ctypes.c_void_p(o), ctypes.c_void_p(stream)))
+                                                _dp(us) if us is not None else None, ctypes.c_void_p(o),
+                                                ctypes.c_void_p(stream)))
 
 
 class Plan:
@@ -370,9 +373,10 @@ class Forest:
         _check(library().lbm_step_coarse(self.h, n))
 
     def get_macroscopic(self, level, rho=None, u=None, on_device=False):
-        """Returns (rho, u); allocates numpy outputs when none are given and on_device is False."""
+        """Returns (rho, u); allocates numpy outputs when none are given and on_device is False.  level = -1:
+        every level, level 0 first, in one array."""
         if rho is None and u is None and not on_device:
-            n = self.n_cells(level)
+            n = sum(self.n_cells(L) for L in range(self.nlev)) if level == -1 else self.n_cells(level)
             rho, u = np.zeros(n), np.zeros((3, n))
         _check(library().lbm_get_macroscopic(self.h, level, _ptr(rho), _ptr(u), 1 if on_device else 0))
         return rho, u

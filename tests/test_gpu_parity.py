@@ -557,3 +557,96 @@ def test_full_size_bench_workload_conserves_mass_and_symmetry(lbm):
     g.step_coarse(40)
     m1 = g.reduce_mass_momentum()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-6
+
+
+# --------------------------------------------------------------------------- B = 32
+
+def _macro_errors(f, o):
+    """Velocity error (L-inf over owned fluid cells of every level, relative to the oracle's max |u|)
+    and density error (L-inf) of forest f against the oracle's state."""
+    du, dr, umax = 0.0, 0.0, 0.0
+    for L in range(f.nlev):
+        rho, u = f.get_macroscopic(L)
+        X, Y, Z = f.cell_coords(L)
+        idx = o.lookup(L, X, Y, Z)
+        orho, ou = o.macro(L)
+        ok = np.isfinite(orho[idx])
+        assert (np.isfinite(rho) == ok).all()
+        du = max(du, max(float(np.abs(u[k][ok] - ou[k][idx][ok]).max()) for k in range(3)))
+        dr = max(dr, float(np.abs(rho[ok] - orho[idx][ok]).max()))
+        umax = max(umax, max(float(np.abs(ou[k][idx][ok]).max()) for k in range(3)))
+    return du / umax, dr
+
+
+def test_b32_refined_box_with_a_sphere_on_the_interface_matches_the_oracle(lbm, oracle_mod):
+    """32^3-cell blocks (the block size every bench workload uses): a periodic 64^3 box of 2^3 roots,
+    one corner root refined, a sphere cut by the level interface, Taylor-Green flow; FP64 element by
+    element after 20 coarse steps, in the default launch configuration and with one cell per thread
+    on 2 CTAs per SM."""
+    case = inputs.periodic_case(n=64, B=32, collision="trt", omega=1.7,
+                                regions=[("box", 1, (0, 0, 0), (16, 16, 16))], lmax=1)
+    case["spheres"] = [(16.0, 16.0, 16.0, 6.0)]
+    field = inputs.taylor_green_field(64)
+    o = oracle_mod.Oracle(case)
+    o.init_fields(field)
+    o.step(20)
+    for cfg in (None, (0, 2)):
+        f = lbm.Forest(case, precision="fp64")
+        assert f.nlev == 2
+        if cfg:
+            f.set_kernel_config(*cfg)
+        f.init_fields(field)
+        f.step_coarse(20)
+        assert _compare(f, o) < TOL64
+        f.close()
+
+
+def test_full_size_bench_workload_matches_the_oracle(lbm, oracle_mod):
+    """The bench workload itself (sphere channel, 8.39M cells, 4 levels, 32^3 blocks, periodic,
+    plug start) in the launch configuration bench.py times: FP64 equals the oracle element by
+    element to 1e-12 after 4 coarse steps (60 level launches, 28 explosions).  The FP32S and FP16S
+    storage (shifted by f^eq(rho0, plug)) against the same oracle state: velocity error relative to
+    the largest oracle speed, and density error."""
+    case = inputs.sphere_channel_case()
+    steps = 4
+    o = oracle_mod.Oracle(case)
+    o.init_fields(inputs.uniform_field(u=case["u_init"]))
+    o.step(steps)
+    f = lbm.Forest(case, precision="fp64")
+    assert f.nlev == 4 and [len(f.block_table(L)) for L in range(4)] == [16, 120, 56, 64]
+    f.init_uniform(case["u_init"])
+    f.step_coarse(steps)
+    assert _compare(f, o) < TOL64
+    f.close()
+    errs = {}
+    for prec in ("fp32s", "fp16s"):
+        g = lbm.Forest(case, precision=prec)
+        g.init_uniform(case["u_init"])
+        g.step_coarse(steps)
+        errs[prec] = _macro_errors(g, o)
+        g.close()
+    print("B=32 bench workload, %d coarse steps: (u L-inf / u_max, rho L-inf) fp32s %.3e %.3e, fp16s %.3e %.3e"
+          % ((steps,) + errs["fp32s"] + errs["fp16s"]))
+    assert errs["fp32s"][0] < 1e-5 and errs["fp32s"][1] < 1e-6
+    assert errs["fp16s"][0] < 1e-3 and errs["fp16s"][1] < 1e-4
+
+
+def test_macroscopic_fields_of_all_levels_in_one_call(lbm):
+    """level = -1 returns every level in one array, level 0 first: the same values as the per-level
+    calls, on the host and on the device."""
+    import torch
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    f = lbm.Forest(case, precision="fp32s")
+    f.init_uniform(case["u_init"])
+    f.step_coarse(3)
+    per = [f.get_macroscopic(L) for L in range(f.nlev)]
+    rho, u = f.get_macroscopic(-1)
+    assert np.array_equal(rho, np.concatenate([r for r, _ in per]), equal_nan=True)
+    assert np.array_equal(u, np.concatenate([v for _, v in per], axis=1), equal_nan=True)
+    n = rho.size
+    dr = torch.empty(n, dtype=torch.float64, device="cuda")
+    du = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    f.get_macroscopic(-1, dr, du, on_device=True)
+    assert np.array_equal(dr.cpu().numpy(), rho, equal_nan=True)
+    assert np.array_equal(du.cpu().numpy(), u, equal_nan=True)
+    f.close()
