@@ -75,41 +75,20 @@ __device__ __forceinline__ double shift_value(int q, double rho0, const double (
 }
 
 // ------------------------------------------------------------------ shared-memory staging
-// Bulk asynchronous copies global -> shared on the TMA engine (the non-tensor form: 16-byte aligned
-// addresses, sizes a multiple of 16 bytes), completing on an mbarrier by transaction count.
-__device__ __forceinline__ uint32_t sh_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(bar)), "r"(count) : "memory");
+// 4-byte asynchronous copies global -> shared (LDGSTS); a false predicate zero-fills without
+// reading global memory.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(pred ? 4 : 0) : "memory");
 }
-__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sh_addr(bar)) : "memory");
-}
-// One arrival that also raises the phase's expected transaction bytes.
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(sh_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sh_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(sh_addr(bar))
-                 : "memory");
-}
-// Orders this thread's generic-proxy shared-memory accesses before later bulk copies into the
-// same bytes.
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Iterations of a bounded mbarrier wait (each try_wait itself blocks for a while): far beyond any
-// copy's completion time; running out marks the launch's error flag.
-constexpr int kWaitIters = 1 << 22;
+// Cells whose pulls are in flight per thread in the FP32 column walk (pipeline depth).
+#ifndef LBM_CP_STAGES
+#define LBM_CP_STAGES 2
+#endif
 
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
 // v holds f (or its shifted form) on entry and f-tilde on exit.  R is rho (or rho - rho0).
