@@ -221,9 +221,13 @@ lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);
 lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level,
                           double* ms_explode_per_level, int64_t* launches_explode_per_level);
 
-/* Thread mapping of the stream-collide kernel (results do not depend on it): each thread walks
- * 2^cells_per_thread_log2 cells (<= B) of one z-column of a block, and the kernel variant is
- * compiled for ctas_per_sm (2, 3 or 4) resident 256-thread CTAs per SM.  Synchronises the stream
+/* Thread mapping of the stream-collide kernel (results do not depend on it).  ctas_per_sm (1 to 4)
+ * selects the kernel variant compiled for that many resident 256-thread CTAs per SM (its shared
+ * memory may allow fewer; fewer CTAs stage more planes ahead).  LBM_FP64: each thread walks
+ * 2^cells_per_thread_log2 cells (<= B) of one z-column of a block.  LBM_FP32S / LBM_FP16S: the
+ * column walk is persistent (one grid of resident CTAs that take chunks of planes from a counter)
+ * and each thread updates two x-adjacent cells, so cells_per_thread_log2 is only checked.  The
+ * default is (log2 B - 3, 3) for LBM_FP64 and (log2 B - 3, 2) otherwise.  Synchronises the stream
  * and drops the captured graphs; the next lbm_step_coarse captures them again. */
 lbm_status lbm_set_kernel_config(lbm_forest* f, int32_t cells_per_thread_log2, int32_t ctas_per_sm);
 lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm);
@@ -232,7 +236,7 @@ lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_
 lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n);
 
 /* Picks the fastest thread mapping for this forest: times n_steps coarse steps (Alg. 1) for every
- * (cells_per_thread_log2 <= log2 B, ctas_per_sm in 2..4) pair, applies the fastest as
+ * (cells_per_thread_log2 <= log2 B, ctas_per_sm in 1..4) pair, applies the fastest as
  * lbm_set_kernel_config would, and writes it and its ms per coarse step (outputs may be NULL).
  * The state of the forest (every level's two PDF grids and parities) is copied on the device first
  * and restored afterwards, so the call leaves the simulation where it was; the copy needs as much

@@ -50,9 +50,12 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
 
 struct Launch {
     int level, substep, grid;
-    int type;   // 0: stream-collide F_L(substep), 1: explosion E_L
+    int type;   // 0: stream-collide F_L(substep), 1: explosion E_L, 2: coupled cells and ghost work of
+                // F_L(substep) when its column walk is persistent (launched right before it)
     int lzc;    // log2 cells per thread along z of this level's stream-collide launch
     int tot = 0;   // 1: the level's last sub-step of a coarse step, which records the totals
+    int wctas = 0;   // persistent column walk (FP32/FP16 storage): its CTAs, the whole grid
+    int wslot = 0;   // its pair of work counters in the forest's counter array
 };
 
 struct DevBuf {
@@ -143,6 +146,8 @@ struct lbm_forest {
     double u0[3] = {0.0, 0.0, 0.0};   // storage shift velocity (shifted layouts only)
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;      // side branch: coupled cells and ghost work beside the walk
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     const Launchers* L = nullptr;
     size_t esize = 0;
     std::vector<DevBuf> buf;
@@ -154,6 +159,8 @@ struct lbm_forest {
     std::vector<int> red_grid;
     int red_total = 0;
     double* d_out = nullptr;
+    int* d_wq = nullptr;          // work counters of the persistent walk launches, 2 per launch
+    size_t nwq = 0;
     double* h_out = nullptr;
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -193,6 +200,24 @@ void free_timing(lbm_forest* f) {
     f->tmax = f->tused = 0;
 }
 
+// CTAs of a persistent column walk over `nown` owned bricks of B^3 cells: the `resident` CTAs the
+// GPU holds at once, or fewer when the level has less than one chunk per warp (a chunk: the two
+// cells of each of a warp's 32 threads in 8 planes, B^3 / 512 chunks per brick, 8 warps per CTA).
+int walk_ctas(int nown, int B, int resident) {
+    const int64_t chunks = int64_t(nown) * B * B * B / 512;
+    return int(std::max<int64_t>(1, std::min<int64_t>((chunks + 7) / 8, resident)));
+}
+
+// log2 of the planes of a persistent walk's chunk: 8 planes where every warp of the `wctas` CTAs
+// still gets about six chunks, fewer (down to 1; the kernel raises it to its pipeline depth)
+// where the level is small, so that the warps finish together.
+int chunk_planes_log2(int nown, int LB, int wctas) {
+    const int64_t tasks = int64_t(nown) << (3 * LB - 6);   // warp tasks: 64 cells in one plane
+    int zl = 3;
+    while (zl > 0 && (tasks >> zl) < int64_t(6) * 8 * wctas) zl--;
+    return std::min(zl, LB);
+}
+
 StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     StepArgs a{};
     const int L = l.level, n = f->plan.nlev;
@@ -218,10 +243,12 @@ StepArgs make_args(const lbm_forest* f, const Launch& l, const int* cur) {
     a.obstacle_term = (f->u0[0] != 0.0 || f->u0[1] != 0.0 || f->u0[2] != 0.0) ? 1 : 0;
     for (int k = 0; k < 3; k++) a.two_u0[k] = float(2.0 * f->u0[k]);
     for (int q = 0; q < Q; q++) a.e_two_u0[q] = float(2.0 * (EX[q] * f->u0[0] + EY[q] * f->u0[1] + EZ[q] * f->u0[2]));
+    a.wctas = l.wctas;
+    a.wq = f->d_wq ? f->d_wq + 2 * l.wslot : nullptr;
     return a;
 }
 
-void build_schedule(lbm_forest* f) {
+lbm_status build_schedule(lbm_forest* f) {
     f->sched.clear();
     const int n = f->plan.nlev, B = f->plan.B;
     int sms = 152;
@@ -231,12 +258,21 @@ void build_schedule(lbm_forest* f) {
     }
     auto push = [&](int L, int s) {
         const HostLevel& V = f->plan.lv[L];
+        const int64_t nwork = int64_t(V.gwork[s - 1].size() / 4);
+        if (f->L->persistent) {
+            const int resident = sms * f->L->ctas_per_sm(f->plan.LB, f->minb);
+            const int w = walk_ctas(V.nown, B, resident);
+            const int zl = chunk_planes_log2(V.nown, f->plan.LB, w);
+            const int side = int((V.cwork.size() + 255) / 256) + int((nwork + 255) / 256);
+            if (side > 0) f->sched.push_back({L, s, side, 2, zl, 0, w, int(f->sched.size()) + 1});
+            f->sched.push_back({L, s, w, 0, zl, 0, w, int(f->sched.size())});
+            return;
+        }
         // cells per thread: the largest power of two up to the configured bound that still gives
         // about four waves of CTAs on this level
         int lzc = f->lzc;
         while (lzc > 0 && int64_t(V.nown) * B * B * (B >> lzc) / 256 < int64_t(4) * sms * f->minb) lzc--;
         const int64_t units = int64_t(V.nown) * B * B * (B >> lzc);
-        const int64_t nwork = int64_t(V.gwork[s - 1].size() / 4);
         int grid = int((units + 255) / 256) + int((nwork + 255) / 256) + int((V.cwork.size() + 255) / 256);
         f->sched.push_back({L, s, grid, 0, lzc});
     };
@@ -257,6 +293,16 @@ void build_schedule(lbm_forest* f) {
         push(L, 2);
     };
     rec(0);
+    // work counters of the persistent walks (zero between launches)
+    if (f->L->persistent && f->nwq < 2 * f->sched.size()) {
+        if (f->d_wq) cudaFree(f->d_wq);
+        f->d_wq = nullptr;
+        f->nwq = 0;
+        if (cudaMalloc(&f->d_wq, 2 * f->sched.size() * sizeof(int)) != cudaSuccess)
+            return fail(LBM_ENOMEM, "cannot allocate the walk's work counters");
+        CU(cudaMemset(f->d_wq, 0, 2 * f->sched.size() * sizeof(int)));
+        f->nwq = 2 * f->sched.size();
+    }
     // the last sub-step of each level in the coarse step records the totals of what it writes; the
     // warp layout of what an earlier schedule recorded no longer matches
     f->totals_valid = false;
@@ -266,16 +312,20 @@ void build_schedule(lbm_forest* f) {
             if (f->sched[k].level == L && f->sched[k].type == 0) {
                 Launch& l = f->sched[k];
                 l.tot = 1;
+                if (k > 0 && f->sched[k - 1].type == 2 && f->sched[k - 1].level == L) f->sched[k - 1].tot = 1;
+                // the column walk's warps, then the coupled cells' warps
                 const int64_t units = int64_t(f->plan.lv[L].nown) * B * B * (B >> l.lzc);
-                // the column walk's warps (units / 32), then the coupled cells' warps
-                f->tot_warps[L] = units / 32 + int64_t(f->plan.lv[L].cwork.size() + 255) / 256 * 8;
+                f->tot_warps[L] = (l.wctas ? int64_t(l.wctas) * 8 : units / 32) +
+                                  int64_t(f->plan.lv[L].cwork.size() + 255) / 256 * 8;
                 break;
             }
+    return LBM_OK;
 }
 
 // Enqueues every kernel of one coarse step on stream s; cur holds the two-grid parity of each
 // level and is advanced.  With events, evs[k] is recorded before launch k and evs[k+1] after.
 void enqueue_step(lbm_forest* f, cudaStream_t s, int* cur, cudaEvent_t* evs) {
+    bool joined = true;
     for (size_t k = 0; k < f->sched.size(); k++) {
         const Launch& l = f->sched[k];
         if (evs) cudaEventRecord(evs[k], s);
@@ -283,8 +333,22 @@ void enqueue_step(lbm_forest* f, cudaStream_t s, int* cur, cudaEvent_t* evs) {
             f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], s);
             continue;
         }
+        if (l.type == 2) {
+            // the coupled cells and ghost work of the walk that follows (same parity), on a branch
+            // beside it: they read the same grid and write cells the walk does not
+            cudaEventRecord(f->ev_fork, s);
+            cudaStreamWaitEvent(f->side, f->ev_fork, 0);
+            f->L->side(make_args(f, l, cur), f->plan.d.collision, l.grid, f->side);
+            cudaEventRecord(f->ev_join, f->side);
+            joined = false;
+            continue;
+        }
         StepArgs a = make_args(f, l, cur);
         f->L->step(a, f->plan.d.collision, l.grid, s);
+        if (!joined) {
+            cudaStreamWaitEvent(s, f->ev_join, 0);
+            joined = true;
+        }
         cur[l.level] ^= 1;
     }
     if (evs) cudaEventRecord(evs[f->sched.size()], s);
@@ -337,6 +401,7 @@ lbm_status check_level(const lbm_forest* f, int level) {
 int64_t owned_cells(const lbm_forest* f, int L) {
     return int64_t(f->plan.lv[L].nown) * f->plan.B * f->plan.B * f->plan.B;
 }
+
 
 }  // namespace
 
@@ -445,9 +510,13 @@ lbm_status lbm_destroy(lbm_forest* f) {
     cudaFree(f->d_wall);
     cudaFree(f->d_partial);
     cudaFree(f->d_out);
+    cudaFree(f->d_wq);
     cudaFree(f->d_stage);
     if (f->h_out) cudaFreeHost(f->h_out);
     if (f->cap) cudaStreamDestroy(f->cap);
+    if (f->side) cudaStreamDestroy(f->side);
+    if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+    if (f->ev_join) cudaEventDestroy(f->ev_join);
     delete f;
     return LBM_OK;
 }
@@ -477,6 +546,10 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     };
     if (cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(LBM_ECUDA, "cannot create the capture stream (is a CUDA device present?)"));
+    if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(LBM_ECUDA, "cannot create the side stream"));
     f->buf.resize(P.nlev);
     f->dl.resize(P.nlev);
     for (int L = 0; L < P.nlev; L++) {
@@ -494,9 +567,10 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
             (s = upload(&b.gwork[0], V.gwork[0])) || (s = upload(&b.gwork[1], V.gwork[1])) ||
             (s = upload(&b.ework, V.ework)) || (s = upload(&b.cwork, V.cwork)))
             return bail(s);
-        // per-warp totals of the recording launch, sized for one cell per thread (the most warps),
-        // then the coupled cells' warps
-        const int64_t wmax = (int64_t(V.nown) * B3 + 255) / 256 * 8 + int64_t(V.cwork.size() + 255) / 256 * 8;
+        // per-warp totals of the recording launch, sized for one cell per thread or a persistent walk
+        // of up to 4,096 CTAs (the most warps), then the coupled cells' warps
+        const int64_t wmax = std::max<int64_t>((int64_t(V.nown) * B3 + 255) / 256, 4 * 1024) * 8 +
+                             int64_t(V.cwork.size() + 255) / 256 * 8;
         if (cudaMalloc(&b.wpart, size_t(wmax + 1) * 4 * sizeof(double)) != cudaSuccess)
             return bail(fail(LBM_ENOMEM, "cannot allocate the totals of level %d", L));
         DevLevel& g = f->dl[L];
@@ -554,6 +628,7 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
     if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
         cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
         return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
+    if (f->L->prepare() != cudaSuccess) return bail(fail(LBM_ECUDA, "cannot set the step kernels' shared-memory limit"));
     // host staging of (rho, u) for the largest level, sized once: growing it later would free and
     // allocate device memory (cudaFree synchronises) in the middle of a caller's loop
     {
@@ -562,9 +637,11 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         lbm_status st = ensure_stage(f, size_t(nmax) * 4 * sizeof(double));
         if (st) return bail(st);
     }
-    // cells per thread along z: 4 for 32^3 blocks, 2 for 16^3, 1 for 8^3
+    // cells per thread along z: 4 for 32^3 blocks, 2 for 16^3, 1 for 8^3 (the FP64 walk); the
+    // paired walk of the shifted layouts runs two CTAs per SM with three planes staged ahead
     f->lzc = P.LB - 3;
-    build_schedule(f);
+    f->minb = P.d.precision == LBM_FP64 ? 3 : 2;
+    if ((s = build_schedule(f))) return bail(s);
     *out = f;
     return LBM_OK;
 }
@@ -837,13 +914,12 @@ lbm_status lbm_set_kernel_config(lbm_forest* f, int32_t cells_per_thread_log2, i
     if (!f) return fail(LBM_EINVAL, "forest is NULL");
     if (cells_per_thread_log2 < 0 || cells_per_thread_log2 > f->plan.LB)
         return fail(LBM_EINVAL, "cells per thread must be 2^k with 2^k <= B");
-    if (ctas_per_sm < 2 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 2, 3 or 4");
+    if (ctas_per_sm < 1 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 1, 2, 3 or 4");
     CU(cudaStreamSynchronize(f->stream));
     free_graphs(f);
     f->lzc = cells_per_thread_log2;
     f->minb = ctas_per_sm;
-    build_schedule(f);
-    return LBM_OK;
+    return build_schedule(f);
 }
 
 lbm_status lbm_get_kernel_config(const lbm_forest* f, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm) {
@@ -879,8 +955,9 @@ lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches
             if (l.grid <= 0) continue;
             float t = 0.f;
             CU(cudaEventElapsedTime(&t, f->tev[r * ne + k], f->tev[r * ne + k + 1]));
-            ms[2 * l.level + l.type] += t;
-            cnt[2 * l.level + l.type] += 1;
+            // a side launch is part of its sub-step F_L(s): its time counts with the level's launches
+            ms[2 * l.level + (l.type == 1 ? 1 : 0)] += t;
+            if (l.type != 2) cnt[2 * l.level + l.type] += 1;
         }
     for (int L = 0; L < n; L++) {
         if (ms_per_level) ms_per_level[L] = ms[2 * L];
@@ -961,7 +1038,7 @@ lbm_status tune(const std::vector<lbm_forest*>& fs, cudaStream_t s, int LB, int 
     int bl = LB - 3 > 0 ? LB - 3 : 0, bm = 3;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(LBM_ECUDA, "cudaEventCreate failed");
     for (int lzc = 0; lzc <= LB && !st; lzc++)
-        for (int minb = 2; minb <= 4 && !st; minb++) {
+        for (int minb = 1; minb <= 4 && !st; minb++) {
             if ((st = config(lzc, minb)) || (st = step(1))) break;   // the first step captures the graphs
             if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(LBM_ECUDA, "cudaEventRecord failed");
             if (!st) st = step(n_steps);
@@ -1006,7 +1083,7 @@ extern "C" lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cell
 namespace {
 
 struct BatchPhase {
-    int level, substep, type;   // type 0: stream-collide F_L(substep), 1: explosion E_L
+    int level, substep, type;   // type 0: stream-collide F_L(substep), 1: explosion E_L, 2: side work
     int n = 0, total = 0, grid = 0;
     StepArgs* args[2] = {nullptr, nullptr};   // per level-0 parity
     int* prefix = nullptr;
@@ -1016,6 +1093,7 @@ struct BatchPhase {
 
 struct lbm_batch {
     std::vector<lbm_forest*> fs;
+    int* d_wq = nullptr;   // work counters of the persistent walk phases, 2 per (phase, member)
     cudaStream_t stream = nullptr, cap = nullptr;
     const Launchers* L = nullptr;
     int nlev = 0, LB = 0, collision = 0, sms = 152;
@@ -1038,6 +1116,8 @@ void free_phases(lbm_batch* b) {
         cudaFree(ph.prefix);
     }
     b->phases.clear();
+    cudaFree(b->d_wq);
+    b->d_wq = nullptr;
 }
 
 // The phase list of one coarse step: Alg. 1 over the deepest member; a member without level L has
@@ -1049,6 +1129,7 @@ lbm_status build_phases(lbm_batch* b) {
     // cells per thread per level: the largest up to the configured bound that gives about four
     // waves of CTAs over the whole batch
     std::vector<int> lzc(b->nlev);
+    const int resident = b->sms * b->L->ctas_per_sm(b->LB, b->minb);
     for (int L = 0; L < b->nlev; L++) {
         int64_t bricks = 0;
         for (lbm_forest* f : b->fs)
@@ -1057,20 +1138,29 @@ lbm_status build_phases(lbm_batch* b) {
         while (z > 0 && bricks * B * B * (B >> z) / 256 < int64_t(4) * b->sms * b->minb) z--;
         lzc[L] = z;
     }
-    std::vector<std::pair<int, int>> order;   // (level, substep), substep 0 = explosion
+    std::vector<std::pair<int, int>> order0;   // (level, substep), substep 0 = explosion
     std::function<void(int)> rec = [&](int L) {
         if (L == 0) {
             if (b->nlev > 1) rec(1);
-            order.push_back({0, 1});
+            order0.push_back({0, 1});
             return;
         }
-        order.push_back({L, 0});
+        order0.push_back({L, 0});
         if (L + 1 < b->nlev) rec(L + 1);
-        order.push_back({L, 1});
+        order0.push_back({L, 1});
         if (L + 1 < b->nlev) rec(L + 1);
-        order.push_back({L, 2});
+        order0.push_back({L, 2});
     };
     rec(0);
+    // phases (level, substep, type): a persistent walk's coupled cells and ghost work go first
+    struct Ph {
+        int first, second, type;
+    };
+    std::vector<Ph> order;
+    for (const auto& o : order0) {
+        if (o.second != 0 && b->L->persistent) order.push_back({o.first, o.second, 2});
+        order.push_back({o.first, o.second, o.second == 0 ? 1 : 0});
+    }
     std::vector<std::vector<StepArgs>> hargs[2];
     std::vector<std::vector<int>> hprefix;
     for (int p = 0; p < 2; p++) {
@@ -1087,34 +1177,56 @@ lbm_status build_phases(lbm_batch* b) {
                 lbm_forest* f = b->fs[i];
                 if (L >= f->plan.nlev) continue;
                 const HostLevel& V = f->plan.lv[L];
-                int grid;
+                int grid, wctas = 0, zlb = lzc[L];
                 if (s == 0) {
                     grid = int((V.ework.size() / 4 + 255) / 256);
+                } else if (b->L->persistent) {
+                    wctas = walk_ctas(V.nown, B, resident);
+                    zlb = chunk_planes_log2(V.nown, b->LB, wctas);
+                    grid = o.type == 2 ? int((V.cwork.size() + 255) / 256) + int((V.gwork[s - 1].size() / 4 + 255) / 256)
+                                       : wctas;
                 } else {
                     const int64_t units = int64_t(V.nown) * B * B * (B >> lzc[L]);
                     grid = int((units + 255) / 256) + int((V.gwork[s - 1].size() / 4 + 255) / 256) +
                            int((V.cwork.size() + 255) / 256);
                 }
                 if (grid > 0) {
-                    Launch l{L, s == 0 ? 0 : s, grid, s == 0 ? 1 : 0, lzc[L]};
+                    Launch l{L, s == 0 ? 0 : s, grid, o.type, zlb, 0, wctas};
                     args.push_back(make_args(f, l, cur[i].data()));
                     prefix.push_back(prefix.back() + grid);
                 }
-                if (s != 0) cur[i][L] ^= 1;
+                if (o.type == 0) cur[i][L] ^= 1;
             }
             hargs[p].push_back(args);
             if (p == 0) hprefix.push_back(prefix);
+        }
+    }
+    // work counters: 2 per (walk phase, member), the same for both parities (phases run in order)
+    size_t nwq = 0;
+    for (size_t k = 0; k < order.size(); k++)
+        if (order[k].type == 0) nwq += hargs[0][k].size();
+    if (b->L->persistent && nwq > 0) {
+        if (cudaMalloc(&b->d_wq, 2 * nwq * sizeof(int)) != cudaSuccess)
+            return fail(LBM_ENOMEM, "cannot allocate the batch's work counters");
+        CU(cudaMemset(b->d_wq, 0, 2 * nwq * sizeof(int)));
+        size_t slot = 0;
+        for (size_t k = 0; k < order.size(); k++) {
+            if (order[k].type != 0) continue;
+            for (size_t i = 0; i < hargs[0][k].size(); i++, slot++) {
+                hargs[0][k][i].wq = b->d_wq + 2 * slot;
+                hargs[1][k][i].wq = b->d_wq + 2 * slot;
+            }
         }
     }
     for (size_t k = 0; k < order.size(); k++) {
         BatchPhase ph;
         ph.level = order[k].first;
         ph.substep = order[k].second;
-        ph.type = order[k].second == 0 ? 1 : 0;
+        ph.type = order[k].type;
         ph.n = int(hargs[0][k].size());
         ph.total = hprefix[k].back();
-        const int resident = b->sms * (ph.type == 1 ? 8 : b->minb);
-        ph.grid = std::min(ph.total, resident);
+        const int slots = b->sms * (ph.type == 0 ? b->L->ctas_per_sm(b->LB, b->minb) : 8);
+        ph.grid = std::min(ph.total, slots);
         b->phases.push_back(ph);
         BatchPhase& q = b->phases.back();
         if (ph.n == 0) continue;
@@ -1132,6 +1244,7 @@ lbm_status capture_batch(lbm_batch* b, int parity) {
     for (const BatchPhase& ph : b->phases) {
         if (ph.n == 0) continue;
         if (ph.type == 1) b->L->explode_batch(ph.args[parity], ph.prefix, ph.n, ph.total, ph.grid, b->cap);
+        else if (ph.type == 2) b->L->side_batch(ph.args[parity], ph.prefix, ph.n, ph.total, ph.grid, b->collision, b->LB, b->cap);
         else b->L->step_batch(ph.args[parity], ph.prefix, ph.n, ph.total, ph.grid, b->collision, b->LB, b->minb, b->cap);
     }
     cudaError_t le = cudaGetLastError();
@@ -1191,6 +1304,7 @@ lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** o
     b->LB = f0->plan.LB;
     b->collision = f0->plan.d.collision;
     b->lzc = std::max(0, b->LB - 3);
+    b->minb = f0->plan.d.precision == LBM_FP64 ? 3 : 2;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1205,7 +1319,7 @@ lbm_status lbm_batch_set_kernel_config(lbm_batch* b, int32_t cells_per_thread_lo
     if (!b) return fail(LBM_EINVAL, "batch is NULL");
     if (cells_per_thread_log2 < 0 || cells_per_thread_log2 > b->LB)
         return fail(LBM_EINVAL, "cells per thread must be 2^k with 2^k <= B");
-    if (ctas_per_sm < 2 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 2, 3 or 4");
+    if (ctas_per_sm < 1 || ctas_per_sm > 4) return fail(LBM_EINVAL, "ctas_per_sm must be 1, 2, 3 or 4");
     CU(cudaStreamSynchronize(b->stream));
     free_phases(b);
     b->lzc = cells_per_thread_log2;

@@ -432,6 +432,8 @@ struct Builder {
             }
             if (plain) V.kind[k] |= BK_PLAIN;
         }
+        // the FP32 / FP16 column walk handles plain and bounce-back links only
+        const bool paired = p.d.precision != LBM_FP64;
         V.link.assign(size_t(V.nown) * B3, 0u);
         V.colsolid.assign(size_t(V.nown) * B * B, 0u);
         V.colspec.assign(size_t(V.nown) * B * B, 0);
@@ -446,7 +448,9 @@ struct Builder {
                         if (V.cell[c] != CK_FLUID) {
                             m |= 1u << 31;
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
-                        } else if (coal_bits(V, k, x, y, z)) {   // coupled: its own thread
+                        } else if (coal_bits(V, k, x, y, z) || (paired && (m & 0x7FFFEu) && !(m & (1u << 29)))) {
+                            // coupled: its own thread (coalescence links; with the paired FP32 walk of
+                            // the shifted layouts also every other link that is not a plain bounce-back)
                             V.colsolid[size_t(k) * B * B + size_t(y) * B + x] |= 1u << z;
                             V.cwork.push_back(uint32_t(c));
                         }

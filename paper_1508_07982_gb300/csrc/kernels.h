@@ -61,6 +61,9 @@ struct StepArgs {
     int obstacle_term;    // 1: obstacle bounce-backs add wall row 7 (a nonzero storage shift)
     float two_u0[3];      // 2 u0 and 2 e_a . u0 of the storage shift (FP32 arithmetic; 0 unshifted)
     float e_two_u0[19];
+    int wctas;            // FP32/FP16 storage: the launch's persistent walk CTAs (its whole grid)
+    int* wq;              // FP32/FP16 storage: the walk's chunk counter and finished-CTA counter,
+                          // zero at the launch's start (its last CTA resets them)
 };
 
 // Bits of the per-cell link mask.
@@ -88,6 +91,18 @@ struct Launchers {
     void (*step_batch)(const StepArgs* args, const int* prefix, int n, int total, int grid, int collision, int LB,
                        int minb, cudaStream_t s);
     void (*explode_batch)(const StepArgs* args, const int* prefix, int n, int total, int grid, cudaStream_t s);
+    // Sets the dynamic shared-memory limit of every step-kernel variant; call before launching
+    // or capturing any of them (idempotent).
+    cudaError_t (*prepare)();
+    // CTAs per SM of the step kernel for block size 2^LB and the configured CTAs per SM (the shared
+    // memory may allow fewer), and whether its column walk is persistent (FP32/FP16 storage).
+    int (*ctas_per_sm)(int LB, int minb);
+    bool persistent;
+    // The coupled cells and ghost work of a persistent walk's F_L(s) (side_kernel), `grid` CTAs;
+    // and of a batch of forests, as step_batch.
+    void (*side)(const StepArgs& a, int collision, int grid, cudaStream_t s);
+    void (*side_batch)(const StepArgs* args, const int* prefix, int n, int total, int grid, int collision, int LB,
+                       cudaStream_t s);
 };
 const Launchers& launchers_f64();
 const Launchers& launchers_f32();

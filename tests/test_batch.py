@@ -90,8 +90,9 @@ def test_batch_steps_each_member_as_a_single_forest_would(lbm, precision):
         for L in range(fa.nlev):
             assert _same(fa.get_pdfs(L), fb.get_pdfs(L)), "member differs on level %d" % L
     assert b.cell_updates_per_coarse_step() == sum(f.cell_updates_per_coarse_step() for f in together)
-    # one launch per phase: level 0, and per level L >= 1 its explosions and sub-steps
-    assert b.launches_per_coarse_step() <= 1 + 3 + 6
+    # one launch per phase: level 0, and per level L >= 1 its explosions and sub-steps; with FP32/FP16
+    # storage each sub-step's coupled cells and ghost work take a launch of their own before it
+    assert b.launches_per_coarse_step() <= (1 + 3 + 6) * (1 if precision == "fp64" else 2)
     # members still step on their own afterwards, and the batch picks up where they are
     for f in together:
         f.step_coarse(1)
@@ -137,7 +138,7 @@ def test_autotune_leaves_the_state_and_results_unchanged(lbm):
         h.step_coarse(3)
     before = [f.get_pdfs(L) for L in range(f.nlev)]
     lzc, minb, ms = f.autotune(2)
-    assert 0 <= lzc <= 4 and minb in (2, 3, 4) and ms > 0
+    assert 0 <= lzc <= 4 and minb in (1, 2, 3, 4) and ms > 0
     assert f.kernel_config() == (lzc, minb)
     for L in range(f.nlev):
         assert _same(before[L], f.get_pdfs(L))
@@ -154,7 +155,7 @@ def test_batch_autotune_keeps_members_in_step(lbm):
     ref = _forests(lbm, cases, "fp32s")
     b = lbm.Batch(fs)
     lzc, minb, ms = b.autotune(2)
-    assert 0 <= lzc <= 4 and minb in (2, 3, 4) and ms > 0
+    assert 0 <= lzc <= 4 and minb in (1, 2, 3, 4) and ms > 0
     b.step(5)
     for f in ref:
         f.step_coarse(5)
