@@ -176,10 +176,11 @@ def _timed_graph(f, torch, steps):
 
 def _timed_kernels(f, torch, steps):
     """The same K coarse steps with a CUDA event between every pair of kernels (the launches are
-    enqueued directly in this mode); returns (total ms, per-level kernel times and counts)."""
+    enqueued directly and in series in this mode); returns (total ms, per-level kernel times and
+    counts of the column walk, the explosions and the side kernels)."""
     f.timing_begin(steps)
     ms = _timed_graph(f, torch, steps)
-    return ms, f.timing_end(explode=True)
+    return ms, f.timing_end(explode=True, side=True)
 
 
 def _run_timed(lbm, torch, case, precision, steps, warmup):
@@ -195,7 +196,7 @@ def _run_timed(lbm, torch, case, precision, steps, warmup):
 
 
 def _roofline(f, lev, precision, peaks, peak_kind):
-    ms_l, cnt_l, ems_l, ecnt_l = lev
+    ms_l, cnt_l, ems_l, ecnt_l, sms_l, scnt_l = lev
 
     L = int(np.argmax(ms_l))
     counts = _fluid_counts(f)
@@ -204,23 +205,24 @@ def _roofline(f, lev, precision, peaks, peak_kind):
     achieved = bytes_per_launch / avg_s / 1e9
     peak = float(peaks["hbm_gbs"])
     traffic = _ncu_traffic(precision)
-    total = ms_l.sum() + ems_l.sum()
+    total = ms_l.sum() + ems_l.sum() + sms_l.sum()
     share = ms_l / total
     per_level = [{"level": i, "launches": int(cnt_l[i]), "ms_total": round(float(ms_l[i]), 4),
                   "share": round(float(share[i]), 4), "explode_launches": int(ecnt_l[i]),
-                  "explode_ms_total": round(float(ems_l[i]), 4),
+                  "explode_ms_total": round(float(ems_l[i]), 4), "side_launches": int(scnt_l[i]),
+                  "side_ms_total": round(float(sms_l[i]), 4),
                   "GBps_algorithmic": round(counts[i] * 2 * 19 * BYTES_PER_VALUE[precision] / (ms_l[i] / cnt_l[i] / 1e3) / 1e9, 1)
                   if cnt_l[i] else None} for i in range(f.nlev)]
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": "step_kernel level %d (finest) fused stream-collide" % L,
+            "kernel": "step_kernel level %d fused stream-collide (column walk; its side kernel timed apart)" % L,
             "bytes_per_launch_algorithmic": int(bytes_per_launch),
             "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s",
             "per_level": per_level}
 
 
-# FP64 arithmetic of the FP64 step kernel: 220 FP64 thread instructions per cell update (ncu,
-# profiles/step_kernel_sphere_channel_fp64.md).  Peak: 2 per clock per SM (the nominal 1.25 TFLOP/s
+# FP64 arithmetic of the FP64 step kernel: 220 FP64 thread instructions per cell update (an ncu
+# count of the level-3 launch of this workload).  Peak: 2 per clock per SM (the nominal 1.25 TFLOP/s
 # FP64 of GB300 as FMAs over 152 SMs at 2.07 GHz).
 FP64_INST_PER_UPDATE = 220
 FP64_INST_PEAK_G = 2 * 152 * 2.07
@@ -402,26 +404,65 @@ def _lid(lbm, torch, peaks, peak_kind, steps=100, steps64=20):
     return out
 
 
-def _uniform_grid_leg(lbm, torch, peaks, peak_kind, n=512, steps=100):
-    """The pure stream-collide case: a uniform periodic n^3 grid (one level, 32^3 blocks), SRT
-    omega = 1.9, FP32S, started from the uniform flow (0.02, 0, 0).  No interfaces and no walls:
-    the column walk alone, the kernel's ceiling on the refined workloads."""
+def _taylor_green_on_device(f, torch, N, umax=0.02, sigma=1e-4, seed=None):
+    """The periodic workload's start on the device: the seeded Taylor-Green modes of
+    inputs.taylor_green_modes evaluated at every cell centre and scaled to max |u| = umax, and
+    rho = 1 + N(0, sigma^2) from a seeded torch generator (the parity tests use the counter-based
+    host generator at 64^3; at 512^3 the host would need minutes)."""
+    from paper_1508_07982_gb300 import inputs
+    seed = inputs.SEED if seed is None else seed
+    modes = inputs.taylor_green_modes(seed)
+    bt = torch.as_tensor(f.block_table(0), device="cuda", dtype=torch.float64)
+    B = f.B
+    r = torch.arange(B, device="cuda", dtype=torch.float64) + 0.5
+    lz, ly, lx = torch.meshgrid(r, r, r, indexing="ij")
+    X = (bt[:, 0:1] * B + lx.reshape(1, -1)).reshape(-1) * (2.0 * np.pi / N)
+    Y = (bt[:, 1:2] * B + ly.reshape(1, -1)).reshape(-1) * (2.0 * np.pi / N)
+    Z = (bt[:, 2:3] * B + lz.reshape(1, -1)).reshape(-1) * (2.0 * np.pi / N)
+    u = torch.zeros((3, X.numel()), dtype=torch.float64, device="cuda")
+    for k, a in modes:
+        sx, cx = torch.sin(k[0] * X), torch.cos(k[0] * X)
+        sy, cy = torch.sin(k[1] * Y), torch.cos(k[1] * Y)
+        sz, cz = torch.sin(k[2] * Z), torch.cos(k[2] * Z)
+        u[0] += a[0] * cx * sy * sz
+        u[1] += a[1] * sx * cy * sz
+        u[2] += a[2] * sx * sy * cz
+    del X, Y, Z
+    u *= umax / float(torch.sqrt((u * u).sum(0)).max())
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    rho = 1.0 + sigma * torch.randn(u.shape[1], dtype=torch.float64, device="cuda", generator=g)
+    f.init_equilibrium(0, rho, u, on_device=True)
+    torch.cuda.synchronize()
+
+
+def _uniform_grid_leg(lbm, torch, peaks, peak_kind, n=512, steps=200):
+    """The pure stream-collide case of the periodic workload: a uniform periodic n^3 grid (one level,
+    32^3 blocks), SRT omega = 1.9, from the seeded Taylor-Green start with density noise, `steps`
+    steps per precision (FP32S, FP16S and FP64).  No interfaces and no walls: the column walk
+    alone."""
     from paper_1508_07982_gb300 import inputs
     case = inputs.periodic_case(n=n, B=32, collision="srt", omega=1.9)
-    f = lbm.Forest(case, precision="fp32s")
-    f.init_uniform((0.02, 0.0, 0.0))
-    f.step_coarse(3)
-    torch.cuda.synchronize()
-    ms = _timed_graph(f, torch, steps)
-    _, lev = _timed_kernels(f, torch, steps)
-    upd = f.cell_updates_per_coarse_step()
-    r = _roofline(f, lev, "fp32s", peaks, peak_kind)
-    out = {"workload": "uniform periodic %d^3 (one level, 32^3 blocks), SRT omega 1.9, FP32S, uniform start (0.02, 0, 0)" % n,
-           "value": round(upd * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms / steps, 5),
-           "steps": steps,
-           "roofline": dict({kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac")}, traffic=None,
-                            kernel="step_kernel level 0 (the only level)")}
-    f.close()
+    out = {"workload": "uniform periodic %d^3 (one level, 32^3 blocks), SRT omega 1.9, Taylor-Green modes "
+                       "k <= 4 scaled to max |u| 0.02 plus N(0, 1e-4) density noise, %d steps" % (n, steps)}
+    for prec in ("fp32s", "fp16s", "fp64"):
+        f = lbm.Forest(case, precision=prec)
+        _taylor_green_on_device(f, torch, n)
+        torch.cuda.synchronize()
+        ms = _timed_graph(f, torch, steps)
+        _taylor_green_on_device(f, torch, n)
+        _, lev = _timed_kernels(f, torch, steps)
+        upd = f.cell_updates_per_coarse_step()
+        r = _roofline(f, lev, prec, peaks, peak_kind)
+        entry = {"value": round(upd * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms / steps, 5),
+                 "steps": steps,
+                 "roofline": dict({kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac")}, traffic=None,
+                                  kernel="step_kernel level 0 (the only level)")}
+        if prec == "fp64":
+            entry["roofline_alu"] = _fp64_alu_roofline(r)
+        out[prec] = entry
+        f.close()
+    # the FP32S figures at the top level, as before
+    out.update({k: out["fp32s"][k] for k in ("value", "unit", "ms_per_step", "steps", "roofline")})
     return out
 
 

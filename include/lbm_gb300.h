@@ -212,14 +212,17 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]);
 
 /* ---- measurement -------------------------------------------------------------------------
  * lbm_timing_begin(f, max_steps) makes the next lbm_step_coarse calls (at most max_steps
- * coarse steps in total) enqueue the step's kernels directly, with a CUDA event recorded on the
- * forest's stream before and after every kernel (the same launches the captured graph holds).
- * lbm_timing_end synchronises and returns, per level, the summed time in ms and the number of
- * launches of the stream-collide kernels and of the explosion kernels (arrays of length
- * n_levels; any may be NULL), then stops timing. */
+ * coarse steps in total) enqueue the step's kernels directly, one after another on the forest's
+ * stream, with a CUDA event recorded before and after every kernel (the launches the captured
+ * graph holds; the side launches that the graph runs on a branch beside the column walk run here
+ * in series, so that every kernel is timed alone).  lbm_timing_end synchronises and returns, per
+ * level, the summed time in ms and the number of launches of the column-walk (stream-collide)
+ * kernels, of the explosion kernels and of the side kernels (coupled cells and ghost work of the
+ * FP32/FP16 layouts) (arrays of length n_levels; any may be NULL), then stops timing. */
 lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps);
 lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level,
-                          double* ms_explode_per_level, int64_t* launches_explode_per_level);
+                          double* ms_explode_per_level, int64_t* launches_explode_per_level,
+                          double* ms_side_per_level, int64_t* launches_side_per_level);
 
 /* Thread mapping of the stream-collide kernel (results do not depend on it).  ctas_per_sm (1 to 4)
  * selects the kernel variant compiled for that many resident 256-thread CTAs per SM (its shared

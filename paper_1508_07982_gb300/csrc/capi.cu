@@ -333,6 +333,10 @@ void enqueue_step(lbm_forest* f, cudaStream_t s, int* cur, cudaEvent_t* evs) {
             f->L->explode(f->dl[l.level], f->dl[l.level - 1], cur[l.level], cur[l.level - 1], s);
             continue;
         }
+        if (l.type == 2 && evs) {   // timed alone, in series
+            f->L->side(make_args(f, l, cur), f->plan.d.collision, l.grid, s);
+            continue;
+        }
         if (l.type == 2) {
             // the coupled cells and ghost work of the walk that follows (same parity), on a branch
             // beside it: they read the same grid and write cells the walk does not
@@ -942,12 +946,12 @@ lbm_status lbm_timing_begin(lbm_forest* f, int32_t max_steps) {
 }
 
 lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches_per_level, double* ms_explode,
-                          int64_t* launches_explode) {
+                          int64_t* launches_explode, double* ms_side, int64_t* launches_side) {
     if (!f) return fail(LBM_EINVAL, "forest is NULL");
     CU(cudaStreamSynchronize(f->stream));
     const int n = f->plan.nlev;
-    std::vector<double> ms(2 * n, 0.0);
-    std::vector<int64_t> cnt(2 * n, 0);
+    std::vector<double> ms(3 * n, 0.0);
+    std::vector<int64_t> cnt(3 * n, 0);
     const size_t ne = f->sched.size() + 1;
     for (int r = 0; r < f->tused; r++)
         for (size_t k = 0; k + 1 < ne; k++) {
@@ -955,15 +959,16 @@ lbm_status lbm_timing_end(lbm_forest* f, double* ms_per_level, int64_t* launches
             if (l.grid <= 0) continue;
             float t = 0.f;
             CU(cudaEventElapsedTime(&t, f->tev[r * ne + k], f->tev[r * ne + k + 1]));
-            // a side launch is part of its sub-step F_L(s): its time counts with the level's launches
-            ms[2 * l.level + (l.type == 1 ? 1 : 0)] += t;
-            if (l.type != 2) cnt[2 * l.level + l.type] += 1;
+            ms[3 * l.level + l.type] += t;
+            cnt[3 * l.level + l.type] += 1;
         }
     for (int L = 0; L < n; L++) {
-        if (ms_per_level) ms_per_level[L] = ms[2 * L];
-        if (launches_per_level) launches_per_level[L] = cnt[2 * L];
-        if (ms_explode) ms_explode[L] = ms[2 * L + 1];
-        if (launches_explode) launches_explode[L] = cnt[2 * L + 1];
+        if (ms_per_level) ms_per_level[L] = ms[3 * L];
+        if (launches_per_level) launches_per_level[L] = cnt[3 * L];
+        if (ms_explode) ms_explode[L] = ms[3 * L + 1];
+        if (launches_explode) launches_explode[L] = cnt[3 * L + 1];
+        if (ms_side) ms_side[L] = ms[3 * L + 2];
+        if (launches_side) launches_side[L] = cnt[3 * L + 2];
     }
     free_timing(f);
     return LBM_OK;

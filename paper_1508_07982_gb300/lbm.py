@@ -103,7 +103,7 @@ def library():
             "lbm_set_pdfs": [P, ctypes.c_int32, P, ctypes.c_int32],
             "lbm_reduce_mass_momentum": [P, dp],
             "lbm_timing_begin": [P, ctypes.c_int32],
-            "lbm_timing_end": [P, dp, i64p, dp, i64p],
+            "lbm_timing_end": [P, dp, i64p, dp, i64p, dp, i64p],
             "lbm_launches_per_coarse_step": [P, i32p],
             "lbm_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_get_kernel_config": [P, i32p, i32p],
@@ -424,16 +424,21 @@ class Forest:
     def timing_begin(self, max_steps):
         _check(library().lbm_timing_begin(self.h, max_steps))
 
-    def timing_end(self, explode=False):
-        """Per level: (ms, launches) of the stream-collide kernels; with explode=True also the
-        explosion kernels' (ms, launches)."""
-        ms = np.zeros(self.nlev)
-        cnt = np.zeros(self.nlev, np.int64)
-        ems = np.zeros(self.nlev)
-        ecnt = np.zeros(self.nlev, np.int64)
+    def timing_end(self, explode=False, side=False):
+        """Per level: (ms, launches) of the column-walk (stream-collide) kernels; with explode=True
+        also the explosion kernels' (ms, launches); with side=True also the side kernels' (coupled
+        cells and ghost work of the FP32/FP16 layouts)."""
+        out = [np.zeros(self.nlev), np.zeros(self.nlev, np.int64), np.zeros(self.nlev), np.zeros(self.nlev, np.int64),
+               np.zeros(self.nlev), np.zeros(self.nlev, np.int64)]
         i64 = ctypes.POINTER(ctypes.c_int64)
-        _check(library().lbm_timing_end(self.h, _dp(ms), cnt.ctypes.data_as(i64), _dp(ems), ecnt.ctypes.data_as(i64)))
-        return (ms, cnt, ems, ecnt) if explode else (ms, cnt)
+        _check(library().lbm_timing_end(self.h, _dp(out[0]), out[1].ctypes.data_as(i64), _dp(out[2]),
+                                        out[3].ctypes.data_as(i64), _dp(out[4]), out[5].ctypes.data_as(i64)))
+        res = tuple(out[:2])
+        if explode:
+            res += tuple(out[2:4])
+        if side:
+            res += tuple(out[4:6])
+        return res
 
 
 class Batch:

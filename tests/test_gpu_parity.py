@@ -650,3 +650,20 @@ def test_macroscopic_fields_of_all_levels_in_one_call(lbm):
     assert np.array_equal(dr.cpu().numpy(), rho, equal_nan=True)
     assert np.array_equal(du.cpu().numpy(), u, equal_nan=True)
     f.close()
+
+
+def test_timing_api_reports_the_side_kernels_apart(lbm):
+    """FP32S storage: the coupled cells and ghost work of each sub-step run in their own side kernel
+    (on a graph branch beside the column walk); the timing mode runs them in series and reports
+    them per level apart from the walk."""
+    f = lbm.Forest(inputs.cavity_case(), precision="fp32s")
+    f.init_uniform()
+    f.step_coarse(2)
+    f.timing_begin(3)
+    f.step_coarse(3)
+    ms, cnt, ems, ecnt, sms, scnt = f.timing_end(explode=True, side=True)
+    assert cnt.tolist() == [3, 6] and ecnt.tolist() == [0, 3]
+    assert scnt[0] == 3 and scnt[1] > 0          # level 0 has coupled cells, level 1 ghost work
+    assert (sms[scnt > 0] > 0).all() and (ms > 0).all()
+    assert f.launches_per_coarse_step() == 4 + int(scnt.sum()) // 3
+    f.close()
