@@ -221,19 +221,26 @@ def _roofline(f, lev, precision, peaks, peak_kind):
             "per_level": per_level}
 
 
-# FP64 arithmetic of the FP64 step kernel: 220 FP64 thread instructions per cell update (an ncu
-# count of the level-3 launch of this workload).  Peak: 2 per clock per SM (the nominal 1.25 TFLOP/s
-# FP64 of GB300 as FMAs over 152 SMs at 2.07 GHz).
-FP64_INST_PER_UPDATE = 220
-FP64_INST_PEAK_G = 2 * 152 * 2.07
+# FP64 arithmetic of the FP64 step kernel: FP64 thread instructions per cell update, an ncu count
+# (sm__sass_thread_inst_executed_op_fp64_pred_on) of the level-3 launch of this workload divided by
+# its fluid cells.  The peak is measured on the device by lbm_probe_fp64_fma (independent FMA chains
+# on every SM), once per run.
+FP64_INST_PER_UPDATE = 161
+_FP64_PEAK = {}
 
 
-def _fp64_alu_roofline(r):
+def _fp64_peak(lbm):
+    if "g" not in _FP64_PEAK:
+        _FP64_PEAK["g"] = lbm.lbm_probe_fp64_fma(20)
+    return _FP64_PEAK["g"]
+
+
+def _fp64_alu_roofline(r, peak_g):
     """The FP64 kernel against its arithmetic bound, from the same launch timing as r."""
     ach = r["achieved"] / (2 * 19 * 8) * FP64_INST_PER_UPDATE      # GB/s -> G updates/s -> G inst/s
-    return {"bound": "alu", "achieved": round(ach, 1), "peak": FP64_INST_PEAK_G, "unit": "G FP64 inst/s",
-            "frac": round(ach / FP64_INST_PEAK_G, 4),
-            "peak_source": "derived: 2 FP64 thread instructions per clock per SM x 152 SMs x 2.07 GHz"}
+    return {"bound": "alu", "achieved": round(ach, 1), "peak": round(peak_g, 1), "unit": "G FP64 inst/s",
+            "frac": round(ach / peak_g, 4), "instructions_per_update": FP64_INST_PER_UPDATE,
+            "peak_source": "measured: lbm_probe_fp64_fma (FP64 FMA chains on every SM, CUDA events)"}
 
 
 _COUNTS = {}
@@ -458,7 +465,7 @@ def _uniform_grid_leg(lbm, torch, peaks, peak_kind, n=512, steps=200):
                  "roofline": dict({kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac")}, traffic=None,
                                   kernel="step_kernel level 0 (the only level)")}
         if prec == "fp64":
-            entry["roofline_alu"] = _fp64_alu_roofline(r)
+            entry["roofline_alu"] = _fp64_alu_roofline(r, _fp64_peak(lbm))
         out[prec] = entry
         f.close()
     # the FP32S figures at the top level, as before
@@ -611,7 +618,7 @@ def main():
             r = _roofline(g, lev_v, prec, peaks, peak_kind)
             entry["roofline"] = {kk: r[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
             if prec == "fp64":
-                entry["roofline_alu"] = _fp64_alu_roofline(r)
+                entry["roofline_alu"] = _fp64_alu_roofline(r, _fp64_peak(lbm))
                 ref64 = g
             else:
                 entry["error_vs_fp64_after_%d_steps" % (k + 3)] = _precision_error(g, ref64)

@@ -285,6 +285,14 @@ lbm_status lbm_batch_destroy(lbm_batch* b);
  * fluid cell's velocity is not finite (a diverged run). */
 lbm_status lbm_velocity_residual(lbm_forest* f, double* r);
 
+/* FP64 arithmetic peak of the current device, measured: a kernel of independent FP64 fused
+ * multiply-add chains on every SM, timed with CUDA events on `stream` over `reps` launches after
+ * a warm-up.  *gfma = FP64 FMA instructions (thread level) per second / 1e9 (a GFLOP/s figure is
+ * twice that).  This is the roofline denominator of the FP64 column walk, whose update is bound by
+ * the FP64 pipe on this GPU (the paper has no counterpart: it is a measurement of the hardware).
+ * Synchronises the stream. */
+lbm_status lbm_probe_fp64_fma(int32_t reps, double* gfma, void* stream);
+
 /* ---- learned warm start: a 3-D convolutional net -------------------------------------------
  * The paper has no learned component; this net serves the warm start of the refined levels.  It
  * maps the coarse-only solution, upsampled onto a refined block plus a halo, to the refined
@@ -355,6 +363,12 @@ lbm_status lbm_net_train_step(lbm_net* n, const void* x, const float* skip, cons
  * ordered differently.  Calls that wait on the tcgen05 kernel return LBM_ETIMEOUT if one of its
  * bounded waits ran out. */
 lbm_status lbm_net_set_backend(lbm_net* n, int32_t backend);
+/* Test of the timeout path: with on = 1 the tcgen05 convolution issues no tensor-core products and
+ * polls its mbarrier at most 1,024 times, so the wait runs out with nothing asynchronous in flight;
+ * the kernel flags it, releases its tensor memory and returns, and the call that waits on it
+ * (lbm_net_forward, lbm_net_predict, lbm_net_train_step) returns LBM_ETIMEOUT with incomplete
+ * outputs.  on = 0 (the default) restores normal operation.  No GPU fault is involved. */
+lbm_status lbm_net_set_wait_test(lbm_net* n, int32_t on);
 
 /* ---- totals without allocation ------------------------------------------------------------
  * The paper has no counterpart: this entry point serves callers that cannot allocate device

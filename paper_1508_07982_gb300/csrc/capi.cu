@@ -407,6 +407,24 @@ int64_t owned_cells(const lbm_forest* f, int L) {
 }
 
 
+// FP64 arithmetic probe: kProbeChains independent FMA chains per thread (enough to cover the FP64
+// pipe's latency), `iters` FMAs each; the sum is written so that nothing is eliminated.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double* sink) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) x[c] = 1.0 + 1e-9 * (threadIdx.x + c);
+    const double a = 0.999999999, b = 1e-10;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; c++) x[c] = fma(x[c], a, b);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) t += x[c];
+    if (t == 12345.0) *sink = t;   // never true; keeps the chains live
+}
+
 }  // namespace
 
 extern "C" {
@@ -877,6 +895,34 @@ lbm_status lbm_reduce_mass_momentum(lbm_forest* f, double out[4]) {
     for (int k = 0; k < 4; k++) out[k] = f->h_out[k];
     for (int k = 0; k < 4; k++)
         if (!std::isfinite(out[k])) return fail(LBM_ENONFINITE, "non-finite total (component %d)", k);
+    return LBM_OK;
+}
+
+lbm_status lbm_probe_fp64_fma(int32_t reps, double* gfma, void* stream) {
+    if (!gfma || reps < 1) return fail(LBM_EINVAL, "invalid argument");
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* sink = nullptr;
+    CU(cudaMalloc(&sink, sizeof(double)));
+    const int grid = sms * 8, iters = 4096;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, sink);   // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; r++) fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, sink);
+    cudaEventRecord(e1, s);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess) return fail(LBM_ECUDA, "FP64 probe failed: %s", cudaGetErrorString(err));
+    const double fmas = double(reps) * grid * 256.0 * iters * kProbeChains;
+    *gfma = fmas / (double(ms) * 1e-3) / 1e9;
     return LBM_OK;
 }
 

@@ -88,71 +88,68 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------------ collision (Sec. 2, 2.1)
-// v holds f (or its shifted form) on entry and f-tilde on exit.  R is rho (or rho - rho0).
-// SRT: f~ = f - omega (f - f^eq) + F;  TRT: f~ = f - le (f+ - f^eq+) - lo (f- - f^eq-) + F, with
-// f^eq of Eq. (fequ) and F_a = 3 w_a rho0 e_a . a (Sec. 2.1); the velocity inside f^eq is
-// sum_a e_a f_a / rho0, unmodified by the force.
-// The body force enters as fa = 3 rho0 a (three values): F_q = w_q (e_q . fa), F_opp(q) = -F_q.
-// rec(R, jx, jy, jz) receives the post-streaming moments the collision starts from.
-// With FP32 arithmetic (the shifted layouts) v holds f - f^eq(rho0, u0): then R = rho - rho0,
-// j = rho0 (u - u0), and the equilibrium is taken relative to the same shift; two_u0 = 2 u0 and
-// e_two_u0[a] = 2 e_a . u0 (constants of the launch).  u0 = 0 gives the f - w rho0 layout.  FP64
-// arithmetic (unshifted storage) ignores them.
+// v holds f (or its shifted form) on entry and f-tilde on exit.
+//   SRT: f~ = f - omega (f - f^eq) + F;  TRT: f~ = f - le (f+ - f^eq+) - lo (f- - f^eq-) + F,
+// with f^eq of Eq. (fequ) and F_a = 3 w_a rho0 e_a . a (Sec. 2.1); the velocity inside f^eq is
+// sum_a e_a f_a / rho0, unmodified by the force.  SRT is TRT with lo = le.  The body force enters
+// as fa = 3 rho0 a (three values): F_q = w_q (e_q . fa), F_opp(q) = -F_q.
+// The update is taken per opposite pair (q, qbar), with s = f_q + f_qbar and t = f_q - f_qbar:
+//   f~_q = f_q - dp - dm',  f~_qbar = f_qbar - dp + dm',
+//   dp  = le (s/2 - f^eq+_q),  f^eq+_q = w (R - base) + 4.5 w rho0 (e.d)(e.(d + 2 u0)),
+//   dm' = lo t/2 - w e.(3 rho0 lo d + fa),          base = 1.5 rho0 d.(d + 2 u0),
+// where R = sum_a v_a and d = sum_a e_a v_a / rho0.  For FP64 storage v = f, u0 = 0: R = rho,
+// d = u.  The shifted layouts (FP32 arithmetic) hold f - f^eq(rho0, u0): then R = rho - rho0,
+// d = u - u0, and the equilibrium is taken relative to the same shift (two_u0 = 2 u0, a launch
+// constant; 0 for FP64).  rec(R, jx, jy, jz) receives the post-streaming moments the collision
+// starts from.  collide2 computes the same update on two cells at once.
 template <typename C, int COLL, typename Rec>
 __device__ __forceinline__ void collide(C (&v)[19], C le, C lo, const C (&fa)[3], C rho0, C inv_rho0,
-                                        const float (&two_u0)[3], const float (&e_two_u0)[19], Rec&& rec) {
+                                        const float (&two_u0)[3], Rec&& rec) {
     constexpr bool kShift = sizeof(C) == 4;
-    C R = C(0), jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-    for (int q = 0; q < 19; q++) {
-        R += v[q];
-        if (dex(q)) jx += dex(q) > 0 ? v[q] : -v[q];
-        if (dey(q)) jy += dey(q) > 0 ? v[q] : -v[q];
-        if (dez(q)) jz += dez(q) > 0 ? v[q] : -v[q];
-    }
-    rec(R, jx, jy, jz);
-    // d = j / rho0 (u - u0 when shifted): the shifted equilibrium's quadratic terms are
-    // (e.u)^2 - (e.u0)^2 = (e.d)(e.d + 2 e.u0) and u^2 - u0^2 = d.(d + 2 u0)
-    const C ux = jx * inv_rho0, uy = jy * inv_rho0, uz = jz * inv_rho0;
-    C usq = ux * ux + uy * uy + uz * uz;
-    if constexpr (kShift) usq += ux * C(two_u0[0]) + uy * C(two_u0[1]) + uz * C(two_u0[2]);
-    const C base = C(1.5) * rho0 * usq;
-    {
-        const C feq0 = C(dw(0)) * (R - base);
-        v[0] = v[0] - le * (v[0] - feq0);
-    }
+    if (COLL != LBM_TRT) lo = le;
+    C s[19], t[19];   // indexed by the odd member of each opposite pair
 #pragma unroll
     for (int q = 1; q < 19; q += 2) {
-        const int p = q + 1;
-        C eu = C(0);
-        if (dex(q)) eu += dex(q) > 0 ? ux : -ux;
-        if (dey(q)) eu += dey(q) > 0 ? uy : -uy;
-        if (dez(q)) eu += dez(q) > 0 ? uz : -uz;
-        C ea = C(0);
-        if (dex(q)) ea += dex(q) > 0 ? fa[0] : -fa[0];
-        if (dey(q)) ea += dey(q) > 0 ? fa[1] : -fa[1];
-        if (dez(q)) ea += dez(q) > 0 ? fa[2] : -fa[2];
-        const C w = C(dw(q));
-        const C Fq = w * ea;
-        C es = eu;
-        if constexpr (kShift) es += C(e_two_u0[q]);
-        const C eqp = w * (R + rho0 * (C(4.5) * eu * es) - base);
-        const C eqm = w * rho0 * C(3.0) * eu;
-        if (COLL == LBM_TRT) {
-            const C fp = C(0.5) * (v[q] + v[p]);
-            const C fm = C(0.5) * (v[q] - v[p]);
-            const C dp = le * (fp - eqp);
-            const C dm = lo * (fm - eqm);
-            const C a = v[q] - dp - dm + Fq;
-            const C b = v[p] - dp + dm - Fq;
-            v[q] = a;
-            v[p] = b;
-        } else {
-            const C a = v[q] - le * (v[q] - (eqp + eqm)) + Fq;
-            const C b = v[p] - le * (v[p] - (eqp - eqm)) - Fq;
-            v[q] = a;
-            v[p] = b;
+        s[q] = v[q] + v[q + 1];
+        t[q] = v[q] - v[q + 1];
+    }
+    const C R = (((v[0] + s[1]) + (s[3] + s[5])) + ((s[7] + s[9]) + (s[11] + s[13]))) + (s[15] + s[17]);
+    const C jx = (t[1] + t[7]) + ((t[9] + t[11]) + t[13]);
+    const C jy = ((t[3] + t[7]) - t[9]) + (t[15] + t[17]);
+    const C jz = (((t[5] + t[11]) - t[13]) + t[15]) - t[17];
+    rec(R, jx, jy, jz);
+    const C ux = jx * inv_rho0, uy = jy * inv_rho0, uz = jz * inv_rho0;
+    const C wx = kShift ? ux + C(two_u0[0]) : ux, wy = kShift ? uy + C(two_u0[1]) : uy, wz = kShift ? uz + C(two_u0[2]) : uz;
+    const C usq = uz * wz + (uy * wy + ux * wx);
+    const C Rb = R - C(1.5) * rho0 * usq;
+    const C w1 = C(dw(1)), w2 = C(dw(7));
+    const C B1 = -le * w1 * Rb, B2 = -le * w2 * Rb;                        // -le w (R - base)
+    const C K1 = -le * C(4.5) * rho0 * w1, K2 = -le * C(4.5) * rho0 * w2;   // -le 4.5 w rho0
+    const C g3 = C(3.0) * rho0 * lo;
+    const C gx = ux * g3 + fa[0], gy = uy * g3 + fa[1], gz = uz * g3 + fa[2];
+    const C leh = C(0.5) * le, loh = C(0.5) * lo;
+    v[0] = v[0] - le * (v[0] - C(dw(0)) * Rb);
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+        const bool diag = q >= 7;
+        C eu = C(0), ew = C(0), eg = C(0);
+        if (dex(q)) { eu += ux; ew += wx; eg += gx; }   // the first member of a pair has e_x >= 0
+        if (dey(q)) {
+            eu += dey(q) > 0 ? uy : -uy;
+            ew += dey(q) > 0 ? wy : -wy;
+            eg += dey(q) > 0 ? gy : -gy;
         }
+        if (dez(q)) {
+            eu += dez(q) > 0 ? uz : -uz;
+            ew += dez(q) > 0 ? wz : -wz;
+            eg += dez(q) > 0 ? gz : -gz;
+        }
+        const C dp = s[q] * leh + ((eu * ew) * (diag ? K2 : K1) + (diag ? B2 : B1));
+        const C dm = t[q] * loh - (diag ? w2 : w1) * eg;
+        const C a = (v[q] - dp) - dm;
+        const C b = (v[q + 1] - dp) + dm;
+        v[q] = a;
+        v[q + 1] = b;
     }
 }
 
@@ -538,7 +535,7 @@ __device__ __forceinline__ void walk_block(const StepArgs& a, int64_t bid, unsig
                         else v[q] = C(st[q * RS - dex(q)]);
                     }
             }
-            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0, a.two_u0, a.e_two_u0, [&](C R, C jx, C jy, C jz) {
+            collide<C, COLL>(v, le, lo, fa, rho0, inv_rho0, a.two_u0, [&](C R, C jx, C jy, C jz) {
                 if (want_tot) {
                     tot[0][tid] += R;
                     tot[1][tid] += jx;
@@ -1079,7 +1076,7 @@ __device__ __forceinline__ void coupled_block(const StepArgs& a, int64_t v, int6
             if ((mq >> q) & 1u) vv[q] = slow[q][tid];
         const LevelParams* P = a.params;
         const C fa[3] = {Par<C>::fa(P, 0), Par<C>::fa(P, 1), Par<C>::fa(P, 2)};
-        collide<C, COLL>(vv, Par<C>::le(P), Par<C>::lo(P), fa, C(a.rho0), C(a.inv_rho0), a.two_u0, a.e_two_u0,
+        collide<C, COLL>(vv, Par<C>::le(P), Par<C>::lo(P), fa, C(a.rho0), C(a.inv_rho0), a.two_u0,
                          [&](C R, C jx, C jy, C jz) {
                              mom[0] = R;
                              mom[1] = jx;
@@ -1323,11 +1320,9 @@ __global__ void init_kernel(const DevLevel lv, int cur, int LB, const LevelParam
         v[q] = C(Store<T>::shifted ? feq - shift_value(q, rho0, lv.u0) : feq);
     }
     const C fa[3] = {C(P->fa[0]), C(P->fa[1]), C(P->fa[2])};
-    float two_u0[3], e_two_u0[19];
+    float two_u0[3];
     for (int k = 0; k < 3; k++) two_u0[k] = float(2.0 * lv.u0[k]);
-#pragma unroll
-    for (int q = 0; q < 19; q++) e_two_u0[q] = float(2.0 * (dex(q) * lv.u0[0] + dey(q) * lv.u0[1] + dez(q) * lv.u0[2]));
-    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0), two_u0, e_two_u0, [](C, C, C, C) {});
+    collide<C, COLL>(v, C(P->le), C(P->lo), fa, C(rho0), C(1.0 / rho0), two_u0, [](C, C, C, C) {});
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         Store<T>::st(f + q * lv.ncells + i, v[q]);

@@ -28,12 +28,13 @@ EXPORTS = [
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
     "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
-    "lbm_mass_momentum_noalloc", "lbm_autotune", "lbm_batch_create", "lbm_batch_step",
+    "lbm_mass_momentum_noalloc", "lbm_probe_fp64_fma", "lbm_autotune", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_set_kernel_config", "lbm_batch_autotune", "lbm_batch_cell_updates_per_coarse_step",
     "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_num_params", "lbm_net_get_params", "lbm_net_set_params", "lbm_net_forward", "lbm_net_predict",
     "lbm_net_gradient", "lbm_net_get_grads", "lbm_net_train_step", "lbm_velocity_residual",
     "lbm_warmstart_features", "lbm_warmstart_targets", "lbm_warmstart_fields", "lbm_net_set_backend",
+    "lbm_net_set_wait_test",
 ]
 NOALLOC_MAX_CELLS = 16384 * 4096
 
@@ -128,7 +129,9 @@ def library():
             "lbm_net_train_step": [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_float, dp],
             "lbm_velocity_residual": [P, dp],
+            "lbm_probe_fp64_fma": [ctypes.c_int32, dp, P],
             "lbm_net_set_backend": [P, ctypes.c_int32],
+            "lbm_net_set_wait_test": [P, ctypes.c_int32],
             "lbm_warmstart_features": [P, P, i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, P, P, P],
             "lbm_warmstart_targets": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -212,6 +215,16 @@ def make_desc(case, precision="fp64"):
     for a, v in enumerate(case.get("u_shift", (0.0, 0.0, 0.0))):
         d.u_shift[a] = float(v)
     return d
+
+
+def lbm_probe_fp64_fma(reps=20, stream=None):
+    """Measured FP64 FMA rate of the device in G FMA/s (see include/lbm_gb300.h)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    r = ctypes.c_double()
+    _check(library().lbm_probe_fp64_fma(reps, ctypes.byref(r), ctypes.c_void_p(stream)))
+    return r.value
 
 
 def lbm_mass_momentum_noalloc(pdfs, precision, n_cells, rho0, out, stream=None, u_shift=None):
@@ -510,6 +523,9 @@ class Net:
             self.close()
         except Exception:
             pass
+
+    def set_wait_test(self, on):
+        _check(library().lbm_net_set_wait_test(self.h, 1 if on else 0))
 
     def set_backend(self, backend):
         """"tcgen05" (default) or "mma.sync" for the convolutions."""

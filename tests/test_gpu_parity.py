@@ -667,3 +667,34 @@ def test_timing_api_reports_the_side_kernels_apart(lbm):
     assert (sms[scnt > 0] > 0).all() and (ms > 0).all()
     assert f.launches_per_coarse_step() == 4 + int(scnt.sum()) // 3
     f.close()
+
+
+def test_a_non_finite_value_is_reported_by_the_totals(lbm):
+    """Failure detection on the host: a NaN written into one fluid cell through lbm_set_pdfs (as a
+    diverged run would leave) makes lbm_reduce_mass_momentum return LBM_ENONFINITE after a step,
+    in every storage precision; obstacle cells, which hold NaN by design, do not."""
+    case = inputs.sphere_channel_case(H=32, B=8, radii=(20.0, 12.0, 6.5))
+    for prec in ("fp64", "fp32s", "fp16s"):
+        f = lbm.Forest(case, precision=prec)
+        f.init_uniform(case["u_init"])
+        f.step_coarse(1)
+        f.reduce_mass_momentum()                      # obstacle NaNs are not counted
+        pd = f.get_pdfs(0)
+        fluid = np.flatnonzero(np.isfinite(pd).all(axis=0))
+        pd[5, fluid[len(fluid) // 2]] = np.nan
+        f.set_pdfs(0, pd)
+        with pytest.raises(lbm.LBMError) as ei:
+            f.reduce_mass_momentum()
+        assert ei.value.status == lbm.LBM_ENONFINITE
+        f.step_coarse(1)                              # the NaN spreads to its neighbours
+        with pytest.raises(lbm.LBMError) as ei:
+            f.reduce_mass_momentum()
+        assert ei.value.status == lbm.LBM_ENONFINITE
+        f.close()
+
+
+def test_fp64_probe_measures_a_plausible_rate(lbm):
+    """The FP64 FMA probe that the bench uses as the FP64 walk's roofline: positive and below the
+    nominal FP64 rate of the part with a margin (1.25 TFLOP/s = 625 G FMA/s nominal)."""
+    g = lbm.lbm_probe_fp64_fma(5)
+    assert 50.0 < g < 2000.0

@@ -218,3 +218,31 @@ def test_net_training_reduces_the_loss(lbm):
         last = net.train_step(xd, td, lr=2e-3)
     assert last < 0.2 * first
     net.close()
+
+
+@pytest.mark.gpu
+def test_a_tensor_core_wait_that_runs_out_is_reported(lbm):
+    """Failure detection without a GPU fault: in its wait test the tcgen05 convolution issues no
+    products, so its bounded mbarrier wait runs out with nothing asynchronous in flight.  The kernel
+    flags it and returns; the forward pass returns LBM_ETIMEOUT.  Switched off, the same net on the
+    same input matches the mma.sync path again (the context stays usable)."""
+    import torch
+    rng = _rng(11)
+    layers, cin, cout = 5, 6, 4
+    p = _params(rng, layers, cin, cout)
+    x = _dev(O.bf16(_input(rng, (2, 18, 18, 18), cin)), torch.bfloat16)
+    net = lbm.Net(layers, cin, cout, seed=4)
+    net.set_params(p)
+    net.set_wait_test(True)
+    with pytest.raises(lbm.LBMError) as ei:
+        net.forward(x)
+    assert ei.value.status == lbm.LBM_ETIMEOUT
+    net.set_wait_test(False)
+    a = net.forward(x).float().cpu().numpy()
+    ref = lbm.Net(layers, cin, cout, seed=4)
+    ref.set_backend("mma.sync")
+    ref.set_params(p)
+    b = ref.forward(x).float().cpu().numpy()
+    assert np.abs(a - b).max() <= 2.0 ** -6 * np.abs(b).max()
+    net.close()
+    ref.close()
