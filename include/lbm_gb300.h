@@ -21,8 +21,9 @@
  *    lbm_get_block_table, each block's B^3 cells in x-fastest, then y, then z order.
  *  - Every call returns an lbm_status; no exception crosses the ABI.  On failure,
  *    lbm_last_error() returns a thread-local description.
- *  - Device memory is owned by the forest handle and released by lbm_destroy.
- *    Caller buffers are owned by the caller.  `on_device` = 1 means a pointer is a CUDA
+ *  - Device memory is owned by the forest (batch, net) handle and released by lbm_destroy
+ *    (lbm_batch_destroy, lbm_net_destroy); it comes from the lbm_allocator given at creation,
+ *    or from cudaMalloc without one.  Caller buffers are owned by the caller.  `on_device` = 1 means a pointer is a CUDA
  *    device pointer on the forest's device; 0 means host memory (pinned or pageable).
  *  - `stream` is a cudaStream_t (0 = the legacy default stream).  Calls that launch work
  *    are asynchronous on that stream unless stated otherwise; calls that return host
@@ -48,6 +49,30 @@ typedef enum {
     LBM_ENONFINITE = 6    /* a reduction met a NaN or Inf */
 } lbm_status;
 
+/* Device-memory hook.  A forest, batch or net created with one takes every device buffer it
+ * holds from `alloc` and gives it back through `release`; created with NULL (or alloc = NULL) it
+ * uses cudaMalloc and cudaFree.  The hook lets a host framework own the memory, for example a
+ * caching allocator that already holds the GPU's memory.
+ *   alloc(bytes, stream, user)    returns a device pointer to `bytes` bytes on the current device,
+ *                                 aligned to 256 bytes, or NULL on failure (the call that needed
+ *                                 it then returns LBM_ENOMEM).  `stream` is the object's stream
+ *                                 (cudaStream_t), on which the library orders all use of the
+ *                                 memory; after each allocation the library synchronises it, so
+ *                                 memory still in use by work queued there is never written.
+ *   release(ptr, bytes, stream, user)  takes back a pointer that alloc returned, with its size.
+ *                                 The library first synchronises `stream`, so nothing still
+ *                                 reads or writes the memory.
+ *   user                          passed through unchanged.
+ * Both are called on the thread that makes the creating, reconfiguring or destroying call, never
+ * from a stream callback.  The library copies the struct; the functions and `user` must stay
+ * valid until the object is destroyed.  Pinned host buffers (a few bytes per object) and the
+ * fixed array of lbm_mass_momentum_noalloc do not go through the hook. */
+typedef struct lbm_allocator {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*release)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} lbm_allocator;
+
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_NOSLIP = 1, LBM_BC_VELOCITY = 2, LBM_BC_FREESLIP = 3 } lbm_bc;
 typedef enum { LBM_SRT = 0, LBM_TRT = 1 } lbm_collision;
 
@@ -70,9 +95,10 @@ typedef enum { LBM_FP64 = 0, LBM_FP32S = 1, LBM_FP16S = 2 } lbm_precision;
  *                 face, with the normal component of the direction reversed; beyond several
  *                 faces, the first non-free-slip face in the order z+, z-, y+, y-, x+, x-
  *                 applies, or, if all are free-slip, the reflection in each (an obstacle at
- *                 the mirrored cell bounces the value back instead).  Every leaf touching a
- *                 free-slip face must be of one level (no level interface meets the face):
- *                 lbm_plan_create / lbm_create_forest return LBM_EINVAL otherwise.
+ *                 the mirrored cell bounces the value back instead).  Level interfaces may meet
+ *                 free-slip faces: the reflection also serves the streamed ghost layers 1-2, whose
+ *                 mirrored neighbours hold exploded or streamed values like any other source
+ *                 (Sec. 4.1 extends the boundary treatment to the innermost ghost layers).
  *   bc_velocity   wall velocity of LBM_BC_VELOCITY faces (Sec. 5.2: velocity bounce-back)
  *   rho0          reference density of the incompressible equilibrium (Eq. fequ)
  *   spheres       no-slip obstacles (cx, cy, cz, r): a cell whose centre lies inside
@@ -139,10 +165,12 @@ lbm_status lbm_plan_destroy(lbm_plan* p);
 /* ---- forest lifetime --------------------------------------------------------------------
  * lbm_create_forest plans the forest (as lbm_plan_create), allocates both PDF grids of every
  * level on the current CUDA device (two-grid storage, Sec. 4.1), uploads the block tables and
- * binds `stream`.  The state starts undefined; call lbm_set_level_params and
- * lbm_init_equilibrium before stepping.  lbm_destroy frees everything (NULL is a no-op). */
+ * binds `stream`.  `alloc` (NULL: cudaMalloc) supplies that memory and every later buffer of the
+ * forest (residual history, autotuning snapshots, work counters).  The state starts undefined;
+ * call lbm_set_level_params and lbm_init_equilibrium before stepping.  lbm_destroy frees
+ * everything (NULL is a no-op). */
 lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag,
-                             void* user, void* stream, lbm_forest** out);
+                             void* user, void* stream, const lbm_allocator* alloc, lbm_forest** out);
 lbm_status lbm_destroy(lbm_forest* f);
 lbm_status lbm_num_levels(const lbm_forest* f, int32_t* n_levels);
 
@@ -256,8 +284,8 @@ lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cells_per_threa
  * GPU with one launch instead of one per member.  Members without level L have no work in the
  * phases of level L.  Each member computes exactly what lbm_step_coarse computes for it.
  *
- * lbm_batch_create(forests, n, out): the members must share precision, collision model, block
- * size and stream; they stay owned by the caller, stay usable through every lbm_* call, and must
+ * lbm_batch_create(forests, n, alloc, out): the members must share precision, collision model,
+ * block size and stream; the batch's own launch tables come from `alloc` (NULL: cudaMalloc); they stay owned by the caller, stay usable through every lbm_* call, and must
  * outlive the batch.  The batch reads each member's buffers through pointers taken when it builds
  * its graphs, so it must be destroyed and re-created after a member is re-created.
  * lbm_batch_step(b, n): n coarse steps of every member on the members' stream (graph replay,
@@ -267,7 +295,8 @@ lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cells_per_threa
  * restores every member's state).  lbm_batch_cell_updates_per_coarse_step sums the members' cell
  * updates; lbm_batch_launches_per_coarse_step counts the launches of one coarse step. */
 typedef struct lbm_batch lbm_batch;
-lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** out);
+lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, const lbm_allocator* alloc,
+                            lbm_batch** out);
 lbm_status lbm_batch_step(lbm_batch* b, int32_t n_steps);
 lbm_status lbm_batch_set_kernel_config(lbm_batch* b, int32_t cells_per_thread_log2, int32_t ctas_per_sm);
 lbm_status lbm_batch_autotune(lbm_batch* b, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
@@ -315,7 +344,9 @@ lbm_status lbm_probe_fp64_fma(int32_t reps, double* gfma, void* stream);
  * all; the mean divides by sum(weight) x out_channels) and the gradients of every parameter
  * (lbm_net_get_grads); lbm_net_train_step does forward, gradient and one Adam step (beta 0.9 /
  * 0.999, eps 1e-8) with learning rate lr.  All pointers except the host parameter buffers are
- * device pointers; calls run on `stream` and synchronise it where they return a loss. */
+ * device pointers; calls run on `stream` and synchronise it where they return a loss.  The
+ * parameters, optimiser moments and the activations of the largest volume set seen so far come
+ * from `alloc` (NULL: cudaMalloc); a call on more voxels than before grows the activations. */
 typedef struct lbm_net lbm_net;
 
 /* Data movement of the warm start (device pointers, asynchronous on `stream`).
@@ -345,7 +376,7 @@ lbm_status lbm_warmstart_targets(const double* rho, const double* u, int32_t B, 
 lbm_status lbm_warmstart_fields(const float* pred, int32_t B, int32_t halo, int32_t nblocks, double rho_scale,
                                 double u_scale, double* rho, double* u, void* stream);
 lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_channels, uint64_t seed, void* stream,
-                          lbm_net** out);
+                          const lbm_allocator* alloc, lbm_net** out);
 lbm_status lbm_net_destroy(lbm_net* n);
 lbm_status lbm_net_num_params(const lbm_net* n, int64_t* count);
 lbm_status lbm_net_get_params(const lbm_net* n, float* host);

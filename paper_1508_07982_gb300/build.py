@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + ARCH
 UNITS = ["forest.cpp", "capi.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f16.cu", "noalloc.cu", "net.cu"]
-HEADERS = ["lbm_internal.h", "kernels.h", "step_kernel.cuh", "kernels_impl.cuh"]
+HEADERS = ["lbm_internal.h", "kernels.h", "step_kernel.cuh", "kernels_impl.cuh", "devmem.h"]
 
 
 def _nvcc():

@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "devmem.h"
 #include "kernels.h"
 
 using namespace lbm;
@@ -180,6 +181,7 @@ struct lbm_forest {
     bool totals_valid = false;        // the recorded moments describe the current state
     std::vector<double*> uprev;   // per level, the velocity of the previous residual call
     double* d_rpart = nullptr;    // residual partial sums
+    DevMem mem;                   // device memory: the caller's allocator hook or cudaMalloc
 };
 
 namespace {
@@ -295,10 +297,10 @@ lbm_status build_schedule(lbm_forest* f) {
     rec(0);
     // work counters of the persistent walks (zero between launches)
     if (f->L->persistent && f->nwq < 2 * f->sched.size()) {
-        if (f->d_wq) cudaFree(f->d_wq);
+        f->mem.put(f->d_wq);
         f->d_wq = nullptr;
         f->nwq = 0;
-        if (cudaMalloc(&f->d_wq, 2 * f->sched.size() * sizeof(int)) != cudaSuccess)
+        if (!f->mem.get(&f->d_wq, 2 * f->sched.size() * sizeof(int)))
             return fail(LBM_ENOMEM, "cannot allocate the walk's work counters");
         CU(cudaMemset(f->d_wq, 0, 2 * f->sched.size() * sizeof(int)));
         f->nwq = 2 * f->sched.size();
@@ -379,19 +381,19 @@ lbm_status capture(lbm_forest* f, int parity) {
 
 lbm_status ensure_stage(lbm_forest* f, size_t bytes) {
     if (f->stage_bytes >= bytes) return LBM_OK;
-    if (f->d_stage) cudaFree(f->d_stage);
+    f->mem.put(f->d_stage);
     f->d_stage = nullptr;
     f->stage_bytes = 0;
-    CU(cudaMalloc(&f->d_stage, bytes));
+    if (!f->mem.get(&f->d_stage, bytes)) return fail(LBM_ENOMEM, "cannot allocate %zu bytes of staging", bytes);
     f->stage_bytes = bytes;
     return LBM_OK;
 }
 
 template <typename T>
-lbm_status upload(T** dst, const std::vector<T>& v) {
+lbm_status upload(DevMem& mem, T** dst, const std::vector<T>& v) {
     *dst = nullptr;
     if (v.empty()) return LBM_OK;
-    CU(cudaMalloc(reinterpret_cast<void**>(dst), v.size() * sizeof(T)));
+    if (!mem.get(dst, v.size() * sizeof(T))) return fail(LBM_ENOMEM, "cannot allocate %zu bytes of tables", v.size() * sizeof(T));
     CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
@@ -410,7 +412,9 @@ int64_t owned_cells(const lbm_forest* f, int L) {
 // FP64 arithmetic probe: kProbeChains independent FMA chains per thread (enough to cover the FP64
 // pipe's latency), `iters` FMAs each; the sum is written so that nothing is eliminated.
 constexpr int kProbeChains = 8;
-__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double* sink) {
+__device__ double g_probe_sink;   // written only if the chains reach an impossible value
+
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters) {
     double x[kProbeChains];
 #pragma unroll
     for (int c = 0; c < kProbeChains; c++) x[c] = 1.0 + 1e-9 * (threadIdx.x + c);
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int iters, double* 
     double t = 0.0;
 #pragma unroll
     for (int c = 0; c < kProbeChains; c++) t += x[c];
-    if (t == 12345.0) *sink = t;   // never true; keeps the chains live
+    if (t == 12345.0) g_probe_sink = t;   // never true; keeps the chains live
 }
 
 }  // namespace
@@ -508,32 +512,32 @@ lbm_status lbm_destroy(lbm_forest* f) {
     if (f->stream || f->cap) cudaStreamSynchronize(f->stream);
     free_graphs(f);
     free_timing(f);
+    DevMem& m = f->mem;
     for (DevBuf& b : f->buf) {
-        cudaFree(b.f[0]);
-        cudaFree(b.f[1]);
-        cudaFree(b.cell);
-        cudaFree(b.nbr);
-        cudaFree(b.parent);
-        cudaFree(b.child);
-        cudaFree(b.pos);
-        cudaFree(b.kind);
-        cudaFree(b.link);
-        cudaFree(b.colsolid);
-        cudaFree(b.colspec);
-        cudaFree(b.gwork[0]);
-        cudaFree(b.gwork[1]);
-        cudaFree(b.ework);
-        cudaFree(b.cwork);
-        cudaFree(b.wpart);
+        for (const void* p : {b.f[0], b.f[1]}) m.put(p);
+        m.put(b.cell);
+        m.put(b.nbr);
+        m.put(b.parent);
+        m.put(b.child);
+        m.put(b.pos);
+        m.put(b.kind);
+        m.put(b.link);
+        m.put(b.colsolid);
+        m.put(b.colspec);
+        m.put(b.gwork[0]);
+        m.put(b.gwork[1]);
+        m.put(b.ework);
+        m.put(b.cwork);
+        m.put(b.wpart);
     }
-    for (double* p : f->uprev) cudaFree(p);
-    cudaFree(f->d_rpart);
-    cudaFree(f->d_params);
-    cudaFree(f->d_wall);
-    cudaFree(f->d_partial);
-    cudaFree(f->d_out);
-    cudaFree(f->d_wq);
-    cudaFree(f->d_stage);
+    for (double* p : f->uprev) m.put(p);
+    m.put(f->d_rpart);
+    m.put(f->d_params);
+    m.put(f->d_wall);
+    m.put(f->d_partial);
+    m.put(f->d_out);
+    m.put(f->d_wq);
+    m.put(f->d_stage);
     if (f->h_out) cudaFreeHost(f->h_out);
     if (f->cap) cudaStreamDestroy(f->cap);
     if (f->side) cudaStreamDestroy(f->side);
@@ -544,7 +548,7 @@ lbm_status lbm_destroy(lbm_forest* f) {
 }
 
 lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag, void* user,
-                             void* stream, lbm_forest** out) {
+                             void* stream, const lbm_allocator* alloc, lbm_forest** out) {
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     lbm_forest* f = new (std::nothrow) lbm_forest;
@@ -555,6 +559,10 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         return fail(LBM_EINVAL, "%s", err.c_str());
     }
     f->stream = static_cast<cudaStream_t>(stream);
+    if (!f->mem.bind(alloc, f->stream)) {
+        delete f;
+        return fail(LBM_EINVAL, "an allocator hook with alloc needs release");
+    }
     f->L = &launchers_for(f->plan.d.precision);
     f->esize = elem_size(f->plan.d.precision);
     const Plan& P = f->plan;
@@ -579,21 +587,23 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         DevBuf& b = f->buf[L];
         const int64_t ncells = int64_t(V.nbricks()) * B3;
         for (int k = 0; k < 2; k++)
-            if (ncells && cudaMalloc(&b.f[k], size_t(ncells) * Q * f->esize) != cudaSuccess)
+            if (!f->mem.get(&b.f[k], size_t(ncells) * Q * f->esize))
                 return bail(fail(LBM_ENOMEM, "cannot allocate %lld bytes of PDFs on level %d",
                                  (long long)(ncells * Q * f->esize), L));
         lbm_status s;
-        if ((s = upload(&b.cell, V.cell)) || (s = upload(&b.nbr, V.nbr)) || (s = upload(&b.parent, V.parent)) ||
-            (s = upload(&b.child, V.child)) || (s = upload(&b.pos, V.pos)) || (s = upload(&b.kind, V.kind)) ||
-            (s = upload(&b.link, V.link)) || (s = upload(&b.colsolid, V.colsolid)) || (s = upload(&b.colspec, V.colspec)) ||
-            (s = upload(&b.gwork[0], V.gwork[0])) || (s = upload(&b.gwork[1], V.gwork[1])) ||
-            (s = upload(&b.ework, V.ework)) || (s = upload(&b.cwork, V.cwork)))
+        DevMem& m = f->mem;
+        if ((s = upload(m, &b.cell, V.cell)) || (s = upload(m, &b.nbr, V.nbr)) || (s = upload(m, &b.parent, V.parent)) ||
+            (s = upload(m, &b.child, V.child)) || (s = upload(m, &b.pos, V.pos)) || (s = upload(m, &b.kind, V.kind)) ||
+            (s = upload(m, &b.link, V.link)) || (s = upload(m, &b.colsolid, V.colsolid)) ||
+            (s = upload(m, &b.colspec, V.colspec)) || (s = upload(m, &b.gwork[0], V.gwork[0])) ||
+            (s = upload(m, &b.gwork[1], V.gwork[1])) || (s = upload(m, &b.ework, V.ework)) ||
+            (s = upload(m, &b.cwork, V.cwork)))
             return bail(s);
         // per-warp totals of the recording launch, sized for one cell per thread or a persistent walk
         // of up to 4,096 CTAs (the most warps), then the coupled cells' warps
         const int64_t wmax = std::max<int64_t>((int64_t(V.nown) * B3 + 255) / 256, 4 * 1024) * 8 +
                              int64_t(V.cwork.size() + 255) / 256 * 8;
-        if (cudaMalloc(&b.wpart, size_t(wmax + 1) * 4 * sizeof(double)) != cudaSuccess)
+        if (!f->mem.get(&b.wpart, size_t(wmax + 1) * 4 * sizeof(double)))
             return bail(fail(LBM_ENOMEM, "cannot allocate the totals of level %d", L));
         DevLevel& g = f->dl[L];
         g.f[0] = b.f[0];
@@ -636,9 +646,9 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
             wall[face * Q + q] = 6.0 * weight(q) * P.d.rho0 * (EX[q] * uw[0] + EY[q] * uw[1] + EZ[q] * uw[2]);
     }
     lbm_status s;
-    if ((s = upload(&f->d_wall, wall))) return bail(s);
+    if ((s = upload(f->mem, &f->d_wall, wall))) return bail(s);
     f->hp.assign(P.nlev, LevelParams{});
-    if (cudaMalloc(&f->d_params, sizeof(LevelParams) * P.nlev) != cudaSuccess)
+    if (!f->mem.get(&f->d_params, sizeof(LevelParams) * P.nlev))
         return bail(fail(LBM_ENOMEM, "cannot allocate level parameters"));
     // reduction scratch: a fixed number of CTAs per level, so totals are summed in a fixed order
     f->red_grid.assign(P.nlev, 0);
@@ -647,8 +657,8 @@ lbm_status lbm_create_forest(const lbm_forest_desc* d, lbm_refine_fn refine, lbm
         f->red_grid[L] = int(std::min<int64_t>((n + 255) / 256, 1216));
         f->red_total += f->red_grid[L];
     }
-    if (cudaMalloc(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) != cudaSuccess ||
-        cudaMalloc(&f->d_out, sizeof(double) * 4) != cudaSuccess || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
+    if (!f->mem.get(&f->d_partial, sizeof(double) * 4 * std::max(f->red_total, 1)) ||
+        !f->mem.get(&f->d_out, sizeof(double) * 4) || cudaMallocHost(&f->h_out, sizeof(double) * 4) != cudaSuccess)
         return bail(fail(LBM_ENOMEM, "cannot allocate reduction buffers"));
     if (f->L->prepare() != cudaSuccess) return bail(fail(LBM_ECUDA, "cannot set the step kernels' shared-memory limit"));
     // host staging of (rho, u) for the largest level, sized once: growing it later would free and
@@ -904,22 +914,19 @@ lbm_status lbm_probe_fp64_fma(int32_t reps, double* gfma, void* stream) {
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    double* sink = nullptr;
-    CU(cudaMalloc(&sink, sizeof(double)));
     const int grid = sms * 8, iters = 4096;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, sink);   // warm-up
+    fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters);   // warm-up
     cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; r++) fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters, sink);
+    for (int r = 0; r < reps; r++) fp64_fma_probe_kernel<<<grid, 256, 0, s>>>(iters);
     cudaEventRecord(e1, s);
     cudaError_t err = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(sink);
     if (err != cudaSuccess) return fail(LBM_ECUDA, "FP64 probe failed: %s", cudaGetErrorString(err));
     const double fmas = double(reps) * grid * 256.0 * iters * kProbeChains;
     *gfma = fmas / (double(ms) * 1e-3) / 1e9;
@@ -932,7 +939,8 @@ lbm_status lbm_velocity_residual(lbm_forest* f, double* r) {
         return fail(LBM_EINVAL, "set the level parameters and initialise every level first");
     const Plan& P = f->plan;
     constexpr int G = 128;
-    if (!f->d_rpart) CU(cudaMalloc(&f->d_rpart, size_t(P.nlev) * G * 4 * sizeof(double)));
+    if (!f->d_rpart && !f->mem.get(&f->d_rpart, size_t(P.nlev) * G * 4 * sizeof(double)))
+        return fail(LBM_ENOMEM, "cannot allocate the residual sums");
     const bool first = f->uprev.empty();
     if (first) f->uprev.assign(P.nlev, nullptr);
     for (int L = 0; L < P.nlev; L++) {
@@ -945,7 +953,12 @@ lbm_status lbm_velocity_residual(lbm_forest* f, double* r) {
         lbm_status s = ensure_stage(f, size_t(n) * 4 * sizeof(double));
         if (s) return s;
         double* st = static_cast<double*>(f->d_stage);
-        if (!f->uprev[L]) CU(cudaMalloc(&f->uprev[L], size_t(n) * 3 * sizeof(double)));
+        if (!f->uprev[L]) {
+            // zeroed: the first call's differences are discarded, but must be finite
+            if (!f->mem.get(&f->uprev[L], size_t(n) * 3 * sizeof(double)))
+                return fail(LBM_ENOMEM, "cannot allocate the residual's velocity history");
+            CU(cudaMemsetAsync(f->uprev[L], 0, size_t(n) * 3 * sizeof(double), f->stream));
+        }
         f->L->macro(f->dl[L], f->cur[L], P.LB, f->d_params + L, P.d.rho0, st, st + n, n, f->stream);
         residual_kernel<<<G, 256, 0, f->stream>>>(st + n, f->uprev[L], f->dl[L].cell, n, std::ldexp(1.0, -3 * L), part);
     }
@@ -1029,6 +1042,7 @@ namespace {
 // state as they found it.
 struct Snapshot {
     std::vector<void*> bufs;
+    std::vector<DevMem*> owner;   // the forest whose memory each buffer came from
     std::vector<std::vector<int>> cur;
 };
 
@@ -1039,14 +1053,10 @@ lbm_status take_snapshot(const std::vector<lbm_forest*>& fs, cudaStream_t s, Sna
             const size_t bytes = size_t(f->dl[L].ncells) * Q * f->esize;
             for (int k = 0; k < 2; k++) {
                 void* p = nullptr;
-                if (bytes) {
-                    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-                        sn.bufs.push_back(nullptr);
-                        return fail(LBM_ENOMEM, "cannot allocate the autotuning snapshot");
-                    }
-                    CU(cudaMemcpyAsync(p, f->dl[L].f[k], bytes, cudaMemcpyDeviceToDevice, s));
-                }
+                if (!f->mem.get(&p, bytes)) return fail(LBM_ENOMEM, "cannot allocate the autotuning snapshot");
                 sn.bufs.push_back(p);
+                sn.owner.push_back(&f->mem);
+                if (bytes) CU(cudaMemcpyAsync(p, f->dl[L].f[k], bytes, cudaMemcpyDeviceToDevice, s));
             }
         }
     }
@@ -1069,8 +1079,9 @@ lbm_status restore_snapshot(const std::vector<lbm_forest*>& fs, cudaStream_t s, 
 }
 
 void free_snapshot(Snapshot& sn) {
-    for (void* p : sn.bufs) cudaFree(p);
+    for (size_t k = 0; k < sn.bufs.size(); k++) sn.owner[k]->put(sn.bufs[k]);
     sn.bufs.clear();
+    sn.owner.clear();
 }
 
 // Times n_steps of `step` for every (cells per thread, CTAs per SM) the kernels support and
@@ -1152,6 +1163,7 @@ struct lbm_batch {
     std::vector<BatchPhase> phases;
     cudaGraphExec_t exec[2] = {};
     int64_t updates = 0;
+    DevMem mem;            // device memory: the caller's allocator hook or cudaMalloc
 };
 
 namespace {
@@ -1162,12 +1174,12 @@ void free_phases(lbm_batch* b) {
         b->exec[p] = nullptr;
     }
     for (BatchPhase& ph : b->phases) {
-        cudaFree(ph.args[0]);
-        cudaFree(ph.args[1]);
-        cudaFree(ph.prefix);
+        b->mem.put(ph.args[0]);
+        b->mem.put(ph.args[1]);
+        b->mem.put(ph.prefix);
     }
     b->phases.clear();
-    cudaFree(b->d_wq);
+    b->mem.put(b->d_wq);
     b->d_wq = nullptr;
 }
 
@@ -1257,7 +1269,7 @@ lbm_status build_phases(lbm_batch* b) {
     for (size_t k = 0; k < order.size(); k++)
         if (order[k].type == 0) nwq += hargs[0][k].size();
     if (b->L->persistent && nwq > 0) {
-        if (cudaMalloc(&b->d_wq, 2 * nwq * sizeof(int)) != cudaSuccess)
+        if (!b->mem.get(&b->d_wq, 2 * nwq * sizeof(int)))
             return fail(LBM_ENOMEM, "cannot allocate the batch's work counters");
         CU(cudaMemset(b->d_wq, 0, 2 * nwq * sizeof(int)));
         size_t slot = 0;
@@ -1282,8 +1294,8 @@ lbm_status build_phases(lbm_batch* b) {
         BatchPhase& q = b->phases.back();
         if (ph.n == 0) continue;
         lbm_status st;
-        if ((st = upload(&q.args[0], hargs[0][k])) || (st = upload(&q.args[1], hargs[1][k])) ||
-            (st = upload(&q.prefix, hprefix[k])))
+        if ((st = upload(b->mem, &q.args[0], hargs[0][k])) || (st = upload(b->mem, &q.args[1], hargs[1][k])) ||
+            (st = upload(b->mem, &q.prefix, hprefix[k])))
             return st;
     }
     return LBM_OK;
@@ -1323,7 +1335,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     return LBM_OK;
 }
 
-lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** out) {
+lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, const lbm_allocator* alloc, lbm_batch** out) {
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!forests || n < 1) return fail(LBM_EINVAL, "a batch needs at least one forest");
@@ -1351,6 +1363,10 @@ lbm_status lbm_batch_create(lbm_forest* const* forests, int32_t n, lbm_batch** o
         b->updates += f->updates;
     }
     b->stream = f0->stream;
+    if (!b->mem.bind(alloc, b->stream)) {
+        delete b;
+        return fail(LBM_EINVAL, "an allocator hook with alloc needs release");
+    }
     b->L = f0->L;
     b->LB = f0->plan.LB;
     b->collision = f0->plan.d.collision;

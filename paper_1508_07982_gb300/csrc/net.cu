@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "devmem.h"
 #include "lbm_internal.h"
 
 namespace {
@@ -433,6 +434,7 @@ struct lbm_net {
     int wait_test = 0;       // 1: the tcgen05 kernel issues no products, so its bounded wait runs out
     int sms = 0;
     Dims d{};
+    lbm::DevMem mem;         // device memory: the caller's allocator hook or cudaMalloc
 };
 
 namespace {
@@ -440,10 +442,10 @@ namespace {
 constexpr int PER_LAYER = TAPS * CH * CH + CH;
 
 void free_acts(lbm_net* n) {
-    for (auto* p : n->act) cudaFree(p);
+    for (auto* p : n->act) n->mem.put(p);
     n->act.clear();
-    cudaFree(n->g0);
-    cudaFree(n->g1);
+    n->mem.put(n->g0);
+    n->mem.put(n->g1);
     n->g0 = n->g1 = nullptr;
     n->cap = 0;
 }
@@ -454,11 +456,11 @@ lbm_status ensure_acts(lbm_net* n, long long N) {
     const size_t bytes = size_t(N) * CH * sizeof(__nv_bfloat16);
     for (int l = 0; l <= n->layers; l++) {
         __nv_bfloat16* p = nullptr;
-        NCU(cudaMalloc(&p, bytes));
+        if (!n->mem.get(&p, bytes)) return nfail(LBM_ENOMEM, "cannot allocate the activations");
         n->act.push_back(p);
     }
-    NCU(cudaMalloc(&n->g0, bytes));
-    NCU(cudaMalloc(&n->g1, bytes));
+    if (!n->mem.get(&n->g0, bytes) || !n->mem.get(&n->g1, bytes))
+        return nfail(LBM_ENOMEM, "cannot allocate the activation gradients");
     n->cap = N;
     return LBM_OK;
 }
@@ -554,7 +556,7 @@ lbm_status forward(lbm_net* n, const __nv_bfloat16* x, const Dims& d) {
 extern "C" {
 
 lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_channels, uint64_t seed, void* stream,
-                          lbm_net** out) {
+                          const lbm_allocator* alloc, lbm_net** out) {
     if (!out) return nfail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (layers < 1 || layers > 16 || in_channels < 1 || in_channels > CH || out_channels < 1 || out_channels > CH)
@@ -565,6 +567,10 @@ lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_chann
     n->cin = in_channels;
     n->cout = out_channels;
     n->stream = static_cast<cudaStream_t>(stream);
+    if (!n->mem.bind(alloc, n->stream)) {
+        delete n;
+        return nfail(LBM_EINVAL, "an allocator hook with alloc needs release");
+    }
     const size_t np = size_t(layers) * PER_LAYER;
     // He-uniform initialisation over the fan-in of each layer (27 taps x its input channels);
     // channels beyond a layer's inputs or outputs keep zero weights
@@ -586,12 +592,10 @@ lbm_status lbm_net_create(int32_t layers, int32_t in_channels, int32_t out_chann
         lbm::set_last_error(keep.c_str());
         return s;
     };
-    if (cudaMalloc(&n->params, np * 4) != cudaSuccess || cudaMalloc(&n->grads, np * 4) != cudaSuccess ||
-        cudaMalloc(&n->m, np * 4) != cudaSuccess || cudaMalloc(&n->v, np * 4) != cudaSuccess ||
-        cudaMalloc(&n->wf, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
-        cudaMalloc(&n->wb, size_t(layers) * TAPS * CH * CH * 2) != cudaSuccess ||
-        cudaMalloc(&n->d_loss, sizeof(double)) != cudaSuccess || cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess)
+    if (!n->mem.get(&n->params, np * 4) || !n->mem.get(&n->grads, np * 4) || !n->mem.get(&n->m, np * 4) ||
+        !n->mem.get(&n->v, np * 4) || !n->mem.get(&n->wf, size_t(layers) * TAPS * CH * CH * 2) ||
+        !n->mem.get(&n->wb, size_t(layers) * TAPS * CH * CH * 2) || !n->mem.get(&n->d_loss, sizeof(double)) ||
+        cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess || !n->mem.get(&n->d_err, sizeof(int)))
         return bail(nfail(LBM_ENOMEM, "cannot allocate the net"));
     if (cudaMemcpy(n->params, h.data(), np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(n->m, 0, np * 4) != cudaSuccess || cudaMemset(n->v, 0, np * 4) != cudaSuccess ||
@@ -610,14 +614,11 @@ lbm_status lbm_net_destroy(lbm_net* n) {
     if (!n) return LBM_OK;
     if (n->stream) cudaStreamSynchronize(n->stream);
     free_acts(n);
-    cudaFree(n->params);
-    cudaFree(n->grads);
-    cudaFree(n->m);
-    cudaFree(n->v);
-    cudaFree(n->wf);
-    cudaFree(n->wb);
-    cudaFree(n->d_loss);
-    cudaFree(n->d_err);
+    for (const void* p : {static_cast<const void*>(n->params), static_cast<const void*>(n->grads),
+                          static_cast<const void*>(n->m), static_cast<const void*>(n->v),
+                          static_cast<const void*>(n->wf), static_cast<const void*>(n->wb),
+                          static_cast<const void*>(n->d_loss), static_cast<const void*>(n->d_err)})
+        n->mem.put(p);
     if (n->h_loss) cudaFreeHost(n->h_loss);
     delete n;
     return LBM_OK;

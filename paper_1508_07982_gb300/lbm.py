@@ -67,6 +67,45 @@ REFINE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_
 FLAG_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                            ctypes.c_void_p)
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """lbm_allocator: the device-memory hook of lbm_create_forest, lbm_batch_create and
+    lbm_net_create."""
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("user", ctypes.c_void_p)]
+
+
+def _torch_alloc(nbytes, stream, user):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:        # out of memory (or torch torn down): the library returns LBM_ENOMEM
+        return None
+
+
+def _torch_release(ptr, nbytes, stream, user):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_TORCH_ALLOCATOR = Allocator(ALLOC_FN(_torch_alloc), RELEASE_FN(_torch_release), None)
+
+
+def _allocator(allocator):
+    """"torch" (the default): torch's CUDA caching allocator; None: the library's cudaMalloc; or an
+    Allocator the caller keeps alive for the object's lifetime."""
+    if allocator == "torch":
+        return ctypes.byref(_TORCH_ALLOCATOR)
+    if allocator is None:
+        return None
+    return ctypes.byref(allocator)
+
+
 _lib = None
 
 
@@ -90,7 +129,8 @@ def library():
             "lbm_plan_counts": [P, ctypes.c_int32, i64p],
             "lbm_plan_ghost_work": [P, ctypes.c_int32, i64p],
             "lbm_plan_destroy": [P],
-            "lbm_create_forest": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, P, ctypes.POINTER(P)],
+            "lbm_create_forest": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, P, ctypes.POINTER(Allocator),
+                                  ctypes.POINTER(P)],
             "lbm_destroy": [P],
             "lbm_num_levels": [P, i32p],
             "lbm_get_block_table": [P, ctypes.c_int32, i32p, i32p],
@@ -110,14 +150,15 @@ def library():
             "lbm_get_kernel_config": [P, i32p, i32p],
             "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, dp, P, P],
             "lbm_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
-            "lbm_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P)],
+            "lbm_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(Allocator), ctypes.POINTER(P)],
             "lbm_batch_step": [P, ctypes.c_int32],
             "lbm_batch_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
             "lbm_batch_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
             "lbm_batch_cell_updates_per_coarse_step": [P, i64p],
             "lbm_batch_launches_per_coarse_step": [P, i32p],
             "lbm_batch_destroy": [P],
-            "lbm_net_create": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P, ctypes.POINTER(P)],
+            "lbm_net_create": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, P,
+                               ctypes.POINTER(Allocator), ctypes.POINTER(P)],
             "lbm_net_destroy": [P],
             "lbm_net_num_params": [P, i64p],
             "lbm_net_get_params": [P, P],
@@ -282,9 +323,10 @@ class Plan:
 
 
 class Forest:
-    """A refined-grid simulation on the current CUDA device (lbm_create_forest ... lbm_destroy)."""
+    """A refined-grid simulation on the current CUDA device (lbm_create_forest ... lbm_destroy).
+    Its device memory comes from torch's caching allocator unless `allocator` says otherwise."""
 
-    def __init__(self, case, precision="fp64", refine=None, flag=None, stream=None):
+    def __init__(self, case, precision="fp64", refine=None, flag=None, stream=None, allocator="torch"):
         L = library()
         self.case = case
         self.precision = precision
@@ -295,8 +337,9 @@ class Forest:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         h = ctypes.c_void_p()
+        self._alloc = allocator
         _check(L.lbm_create_forest(ctypes.byref(self._d), self._refine, self._flag, None,
-                                   ctypes.c_void_p(stream), ctypes.byref(h)))
+                                   ctypes.c_void_p(stream), _allocator(allocator), ctypes.byref(h)))
         self.h = h
         n = ctypes.c_int32()
         _check(L.lbm_num_levels(self.h, ctypes.byref(n)))
@@ -458,11 +501,12 @@ class Batch:
     """Independent forests stepped together, one launch per phase (lbm_batch_create ...
     lbm_batch_destroy).  The forests stay usable one by one and must outlive the batch."""
 
-    def __init__(self, forests):
+    def __init__(self, forests, allocator="torch"):
         self.forests = list(forests)
         arr = (ctypes.c_void_p * len(self.forests))(*[f.h.value for f in self.forests])
         h = ctypes.c_void_p()
-        _check(library().lbm_batch_create(arr, len(self.forests), ctypes.byref(h)))
+        self._alloc = allocator
+        _check(library().lbm_batch_create(arr, len(self.forests), _allocator(allocator), ctypes.byref(h)))
         self.h = h
 
     def close(self):
@@ -503,13 +547,14 @@ class Net:
     tensors on the device: inputs BF16 [nvol, D, H, W, 16]; skip, target FP32 [nvol, D, H, W, out];
     weight FP32 [nvol, D, H, W]."""
 
-    def __init__(self, layers=5, in_channels=6, out_channels=4, seed=20150827, stream=None):
+    def __init__(self, layers=5, in_channels=6, out_channels=4, seed=20150827, stream=None, allocator="torch"):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         h = ctypes.c_void_p()
+        self._alloc = allocator
         _check(library().lbm_net_create(layers, in_channels, out_channels, seed, ctypes.c_void_p(stream),
-                                        ctypes.byref(h)))
+                                        _allocator(allocator), ctypes.byref(h)))
         self.h = h
         self.layers, self.in_channels, self.out_channels = layers, in_channels, out_channels
 
