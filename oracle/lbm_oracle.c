@@ -34,7 +34,10 @@
  *    target streams it holds the value of the mirror cell (one step back inside
  *    along each of those faces' normals) in direction a with those normal
  *    components negated (specular reflection; free-slip is named only, Sec. 4.1),
- *    or the bounced value when the mirror cell is an obstacle;
+ *    or the bounced value when the mirror cell is an obstacle; like every boundary
+ *    treatment it serves each cell that streams, owned or in ghost layers 1-2, so level
+ *    interfaces may meet free-slip faces (Sec. 4.1 extends the boundary handling to the
+ *    innermost ghost layers);
  *  - cells covered by a coarser leaf take the flag of the covering coarse cell,
  *    which makes fluid/obstacle marking consistent across interfaces (Sec. 4.1).
  * Every cell that is not an owned fluid cell starts as NaN, so any read of a

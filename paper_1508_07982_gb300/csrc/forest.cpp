@@ -347,31 +347,27 @@ struct Builder {
         return -1;
     }
 
-    // Every leaf that touches a free-slip face has the same level, so that no level interface,
-    // and no ghost cell, meets the face (the reflection then only reads owned cells).
-    bool freeslip_faces_on_one_level(std::string& err) const {
-        for (int f = 0; f < 6; f++) {
-            if (p.d.bc[f] != LBM_BC_FREESLIP) continue;
-            const int a = f >> 1;
-            int seen = -1;
-            for (int L = 0; L < p.nlev; L++) {
-                const int n[3] = {p.lv[L].nb[0], p.lv[L].nb[1], p.lv[L].nb[2]};
-                const int side = (f & 1) ? n[a] - 1 : 0;
-                for (int z = 0; z < n[2]; z++)
-                    for (int y = 0; y < n[1]; y++)
-                        for (int x = 0; x < n[0]; x++) {
-                            const int c[3] = {x, y, z};
-                            if (c[a] != side || state(L, x, y, z) != LEAF) continue;
-                            if (seen >= 0 && seen != L) {
-                                err = "leaves of levels " + std::to_string(seen) + " and " + std::to_string(L) +
-                                      " touch free-slip face " + std::to_string(f) + " (a level interface meets it)";
-                                return false;
-                            }
-                            seen = L;
-                        }
-            }
+    // Free-slip mirror of pull q into cell (x, y, z) of brick k whose source lies beyond free-slip
+    // faces only (wall_face < 0): the source moved back inside along those faces' normals, i.e. the
+    // tangential neighbour, read in direction qm (q with the mirrored components reversed).  mb is
+    // its brick (or an NB_* code) and mc its cell index in the level's grid (-1 for a code).
+    void mirror(const HostLevel& V, int k, int x, int y, int z, int q, int32_t& mb, int64_t& mc, int& qm) const {
+        const int B = p.B, B3 = B * B * B, M = B - 1;
+        const int t[3] = {x, y, z}, e[3] = {EX[q], EY[q], EZ[q]};
+        int m[3], r[3], o[3];
+        for (int a = 0; a < 3; a++) {
+            const int s = t[a] - e[a];
+            const int g = V.pos[3 * k + a] * B + s;
+            const bool beyond = !p.per[a] && (g < 0 || g >= V.N[a]);
+            m[a] = beyond ? t[a] : s;
+            r[a] = beyond ? -e[a] : e[a];
+            o[a] = m[a] < 0 ? -1 : (m[a] > M ? 1 : 0);
         }
-        return true;
+        qm = q;
+        for (int j = 1; j < Q; j++)
+            if (EX[j] == r[0] && EY[j] == r[1] && EZ[j] == r[2]) qm = j;
+        mb = (o[0] | o[1] | o[2]) ? V.nbr[size_t(k) * 27 + 13 + o[0] + 3 * o[1] + 9 * o[2]] : k;
+        mc = mb >= 0 ? int64_t(mb) * B3 + (int64_t(m[2] & M) * B + (m[1] & M)) * B + (m[0] & M) : -1;
     }
 
     // Fast-path bits of an owned cell's link mask m (Sec. 2.2, Eq. ftoc):
@@ -506,13 +502,30 @@ struct Builder {
                         }
                     }
         }
-        // after sub-step 1: the layer-1 values that owned cells pull in sub-step 2
+        // after sub-step 1: the layer-1 values that owned cells pull in sub-step 2, directly or as
+        // the mirror of a free-slip link (Sec. 4.1: the boundary treatment reaches into the ghost
+        // layers where a level interface meets a free-slip face)
         for (int k = 0; k < V.nown; k++)
             for (int z = 0; z < B; z++)
                 for (int y = 0; y < B; y++)
                     for (int x = 0; x < B; x++) {
                         const size_t c = size_t(k) * B3 + (size_t(z) * B + y) * B + x;
                         if (V.cell[c] != CK_FLUID) continue;
+                        const uint32_t cb = coal_bits(V, k, x, y, z);
+                        for (int q = 1; q < Q; q++) {
+                            if (!((V.link[c] >> q) & 1u) || ((cb >> q) & 1u)) continue;
+                            int32_t nb, mb;
+                            int64_t sc, mc;
+                            int qm;
+                            source(V, k, x, y, z, q, nb, sc);
+                            if (nb != NB_WALL || wall_face(V, k, x - EX[q], y - EY[q], z - EZ[q]) >= 0) continue;
+                            mirror(V, k, x, y, z, q, mb, mc, qm);
+                            if (mb < 0) {
+                                err = "a free-slip mirror of an owned cell lies outside the level";
+                                return false;
+                            }
+                            if (mb >= V.nown && V.cell[mc] == CK_GHOST) need[0][mc - g0] |= 1u << qm;
+                        }
                         const uint32_t gq = ghost_src_bits(V, k, x, y, z, V.link[c] & 0x7FFFEu);
                         for (int q = 1; q < Q; q++) {
                             if (!((gq >> q) & 1u)) continue;
@@ -549,10 +562,25 @@ struct Builder {
                     int64_t sc;
                     source(V, k, x, y, z, q, nb, sc);
                     if ((gl >> q) & 1u) {
-                        const bool bounce = nb == NB_WALL || (nb >= 0 && V.cell[sc] == CK_SOLID);
+                        bool bounce = nb == NB_WALL || (nb >= 0 && V.cell[sc] == CK_SOLID);
                         if (nb == NB_WALL && wall_face(V, k, x - EX[q], y - EY[q], z - EZ[q]) < 0) {
-                            err = "a ghost cell meets a free-slip face";
-                            return false;
+                            // free-slip: the mirror's value, exploded (sub-step 1, layer 3), stored
+                            // after its sub-step-1 stream (layers 1-2) or owned; an obstacle there
+                            // bounces the cell's own value back
+                            int32_t mb;
+                            int64_t mc;
+                            int qm;
+                            mirror(V, k, x, y, z, q, mb, mc, qm);
+                            if (mb < 0 || V.cell[mc] == CK_FAR) {
+                                err = "a free-slip mirror of a ghost cell has no value within ghost layer 3";
+                                return false;
+                            }
+                            if (V.cell[mc] != CK_SOLID) {
+                                bounce = false;
+                                special[s][i] |= 1u << q;
+                                if (s == 1 && mb >= V.nown && V.cell[mc] == CK_GHOST) need[0][mc - g0] |= 1u << qm;
+                                continue;
+                            }
                         }
                         if (!bounce) {
                             err = "a needed ghost value has no source within ghost layer 3";
@@ -652,7 +680,6 @@ bool build_plan(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag
     }
     Builder b{p, refine, flag, user};
     if (!b.leaves(err)) return false;
-    if (!b.freeslip_faces_on_one_level(err)) return false;
     for (int L = 0; L < p.nlev; L++)
         if (!b.bricks(L, err)) return false;
     for (int L = 0; L < p.nlev; L++) b.children(L);

@@ -288,34 +288,38 @@ __device__ C pull_general(const StepArgs& a, const Access<T, C>& acc, int brick,
                 }
             }
         }
-        if (face < 0 && owned) {
+        if (face < 0) {
             // every face is free-slip: specular reflection.  The value comes from the tangential
             // neighbour (the source moved back inside along the mirrored axes), in direction q
-            // with those components reversed; an obstacle there bounces it back instead.  The
-            // neighbour is an owned cell of this level (no level interface meets a free-slip face).
+            // with those components reversed; an obstacle there bounces it back instead.  Where a
+            // level interface meets the face the neighbour may be a ghost cell (Sec. 4.1 extends
+            // the boundary treatment to the ghost layers): it then holds the exploded value in
+            // sub-step 1 and in layer 3, and its sub-step-1 stream otherwise, as any source does.
             const int mx = (mirror & 1) ? x : sx, my = (mirror & 2) ? y : sy, mz = (mirror & 4) ? z : sz;
             const int mox = mx < 0 ? -1 : (mx > M ? 1 : 0);
             const int moy = my < 0 ? -1 : (my > M ? 1 : 0);
             const int moz = mz < 0 ? -1 : (mz > M ? 1 : 0);
             const int mb = (mox | moy | moz) ? __ldg(nbr + 13 + mox + 3 * moy + 9 * moz) : brick;
+            if (mb < 0) return qnan<C>();   // never a source: the planner checks every needed mirror
             const int rx = (mirror & 1) ? -ex : ex, ry = (mirror & 2) ? -ey : ey, rz = (mirror & 4) ? -ez : ez;
             int qm = q;
 #pragma unroll
             for (int k = 1; k < 19; k++)
                 if (dex(k) == rx && dey(k) == ry && dez(k) == rz) qm = k;
-            if (mb >= 0) {
-                const int64_t midx = (int64_t(mb) << B3s) + ((mz & M) << (2 * LB)) + ((my & M) << LB) + (mx & M);
-                if (__ldg(a.lv.cell + midx) != CK_SOLID) {
-                    // the shifted layouts store f - f^eq(rho0, u0): f^eq_qm - f^eq_q of the shift is
-                    // w rho0 (1.5 (E' - E) + 1.125 (E'^2 - E^2)) with E = 2 e_q.u0, E' = 2 e_qm.u0
-                    const float E = a.e_two_u0[q], Em = a.e_two_u0[qm];
-                    return acc.load(src, n, qm, midx) +
-                           C(float(dw(q)) * float(a.rho0) * (1.5f * (Em - E) + 1.125f * (Em * Em - E * E)));
-                }
+            const int64_t midx = (int64_t(mb) << B3s) + ((mz & M) << (2 * LB)) + ((my & M) << LB) + (mx & M);
+            const uint8_t mck = __ldg(a.lv.cell + midx);
+            if (mck != CK_SOLID) {
+                if (mck == CK_FAR) return qnan<C>();
+                const C v = (mb >= a.lv.nown && (a.substep == 1 || mck == CK_G3))
+                                ? acc.coarse(mb, mx & M, my & M, mz & M, qm)
+                                : acc.load(src, n, qm, midx);
+                // the shifted layouts store f - f^eq(rho0, u0): f^eq_qm - f^eq_q of the shift is
+                // w rho0 (1.5 (E' - E) + 1.125 (E'^2 - E^2)) with E = 2 e_q.u0, E' = 2 e_qm.u0
+                const float E = a.e_two_u0[q], Em = a.e_two_u0[qm];
+                return v + C(float(dw(q)) * float(a.rho0) * (1.5f * (Em - E) + 1.125f * (Em * Em - E * E)));
             }
             face = 7;   // obstacle at the mirrored cell: bounce-back, obstacle term
         }
-        if (face < 0) face = 7;   // not reached: ghost cells never meet a free-slip face
         const C o = own_exploded ? acc.coarse(brick, x, y, z, qo) : acc.load(src, n, qo, cidx);
         return o + C(__ldg(a.wall + face * 19 + q));
     }

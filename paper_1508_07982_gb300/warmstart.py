@@ -140,6 +140,29 @@ def train(net, data, epochs, lr=2e-3, batch=32, seed=0):
     return losses
 
 
+def mean_loss(net, data, batch=32):
+    """The net's loss (the training objective) averaged over the mini-batches of `data`, without
+    updating it."""
+    x, skip, target, weight = data
+    tot, cnt = 0.0, 0
+    for i in range(0, x.shape[0], batch):
+        sl = slice(i, i + batch)
+        if weight[sl].sum() == 0:
+            continue
+        net.predict(x[sl].contiguous(), skip[sl].contiguous())
+        tot += net.gradient(target[sl].contiguous(), skip[sl].contiguous(), weight[sl].contiguous())
+        cnt += 1
+    return tot / max(cnt, 1)
+
+
+def zero_net(like):
+    """A net of the same shape with every parameter zero: its prediction is the skip term, the
+    sampled coarse solution itself."""
+    z = lbm.Net(like.layers, like.in_channels, like.out_channels)
+    z.set_params(np.zeros(z.num_params(), np.float32))
+    return z
+
+
 def init_warm(net, coarse, fine, case, halo=HALO, use_net=True):
     """Starts every level of `fine` from f^eq of the coarse solution (level 0) or of the net's
     prediction on its blocks (refined levels); with use_net=False the refined levels take the
@@ -161,11 +184,46 @@ def init_warm(net, coarse, fine, case, halo=HALO, use_net=True):
     return time.perf_counter() - t0
 
 
+def level_fields(f):
+    """(rho, u) of every level of f as device tensors, obstacle cells set to (1, 0)."""
+    import torch
+    out = []
+    for L in range(f.nlev):
+        n = f.n_cells(L)
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        u = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        if n:
+            f.get_macroscopic(L, rho, u, on_device=True)
+        out.append((torch.nan_to_num(rho, nan=1.0), torch.nan_to_num(u, nan=0.0)))
+    return out
+
+
+def init_ideal(coarse, fine, case, fields):
+    """The bound of every predictor of the refined levels: level 0 from the coarse solution as in
+    init_warm, every refined level from `fields`, the converged refined solution itself."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for L in range(fine.nlev):
+        if L == 0:
+            x, skip = features(coarse, fine, case, 0, 0)
+            rho, u = lbm.warmstart_fields(skip, case["B"], 0, len(fine.block_table(0)), RHO_SCALE, u_scale(case))
+            fine.init_equilibrium(0, rho, u, on_device=True)
+        elif fine.n_cells(L):
+            fine.init_equilibrium(L, fields[L][0], fields[L][1], on_device=True)
+        else:
+            fine.init_equilibrium(L)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
 def experiment(n_train=16, n_test=4, H=64, B=8, max_steps=6000, epochs=20, max_blocks=384, seed=20150827,
                precision="fp32s", log=print):
     """Trains the net on n_train cases of inputs.warm_cases and compares, on n_test held-out
     cases, the refined solve from rest (cold), from the sampled coarse solution alone, and from
-    the net's prediction (warm); the coarse-only solve and the net's time count for the last two."""
+    the net's prediction (warm); the coarse-only solve and the net's time count for the last two.
+    A fourth start (ideal) takes level 0 from the coarse solution and every refined level from the
+    cold run's converged solution: no predictor of the refined levels can start closer."""
     import torch
     from . import inputs
     cases = inputs.warm_cases(n_train + n_test, seed=seed, H=H, B=B)
@@ -189,22 +247,32 @@ def experiment(n_train=16, n_test=4, H=64, B=8, max_steps=6000, epochs=20, max_b
     losses = train(net, data, epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    log("losses %s" % ["%.4g" % v for v in losses])
+    zero = zero_net(net)
+    fit = {"net": mean_loss(net, data), "coarse_only": mean_loss(zero, data)}
+    log("losses %s; training-set loss %s" % (["%.4g" % v for v in losses], fit))
     tests = []
     for c in cases[n_train:]:
         row = {"spheres": len(c["spheres"]), "re": round(c["re"], 2)}
         coarse = lbm.Forest(coarse_case(c), precision=precision)
         coarse.init_uniform()
         row["coarse"] = steady(coarse, max_steps)
-        for mode in ("cold", "coarse_only", "warm"):
+        converged = None
+        for mode in ("cold", "coarse_only", "warm", "ideal"):
             fine = lbm.Forest(c, precision=precision)
             t_init = 0.0
             if mode == "cold":
                 fine.init_uniform()
+            elif mode == "ideal":
+                t_init = init_ideal(coarse, fine, c, converged)
             else:
                 t_init = init_warm(net, coarse, fine, c, use_net=(mode == "warm"))
             row[mode] = steady(fine, max_steps)
             row[mode]["init_seconds"] = round(t_init, 4)
+            if mode == "cold":
+                converged = level_fields(fine)
+                held = samples(coarse, fine, c, max_blocks=max_blocks, seed=1000)
+                row["heldout_loss"] = {"net": mean_loss(net, held), "coarse_only": mean_loss(zero, held)}
+                del held
             fine.close()
         coarse.close()
         tests.append(row)
@@ -213,8 +281,38 @@ def experiment(n_train=16, n_test=4, H=64, B=8, max_steps=6000, epochs=20, max_b
                        "max_steps": max_steps, "epochs": epochs, "blocks_per_level_sampled": max_blocks,
                        "halo": HALO, "precision": precision, "net": "5 x conv3d 3x3x3, width 16, BF16"},
             "train_seconds": round(t_train, 2), "train_loss": [round(v, 6) for v in losses],
+            "train_set_loss": fit,
             "voxels_trained": int(data[0].shape[0] * data[0].shape[1] * data[0].shape[2] * data[0].shape[3]),
             "generation": gen, "tests": tests}
+
+
+def heldout_gain(n_train=4, H=32, B=8, max_steps=40000, epochs=10, max_blocks=256, seed=20150827,
+                 precision="fp32s"):
+    """The net's gain where it acts, on one held-out case: trains on n_train cases of
+    inputs.warm_cases (targets: each case's refined solution from the coarse-only start), then
+    compares on case n_train the loss of the net's prediction with that of the sampled coarse
+    solution alone (the skip term), both against the converged refined solution."""
+    from . import inputs
+    cases = inputs.warm_cases(n_train + 1, seed=seed, H=H, B=B)
+    net = lbm.Net(5, 6, 4, seed=seed)
+    zero = zero_net(net)
+    sets = []
+    for i, c in enumerate(cases):
+        coarse = lbm.Forest(coarse_case(c), precision=precision)
+        coarse.init_uniform()
+        steady(coarse, max_steps)
+        fine = lbm.Forest(c, precision=precision)
+        init_warm(net, coarse, fine, c, use_net=False)
+        steady(fine, max_steps)
+        sets.append(samples(coarse, fine, c, max_blocks=max_blocks, seed=i))
+        coarse.close()
+        fine.close()
+    import torch
+    data = tuple(torch.cat([d[k] for d in sets[:n_train]]) for k in range(4))
+    losses = train(net, data, epochs)
+    held = sets[n_train]
+    return {"train_loss": losses, "train_set": {"net": mean_loss(net, data), "coarse_only": mean_loss(zero, data)},
+            "heldout": {"net": mean_loss(net, held), "coarse_only": mean_loss(zero, held)}}
 
 
 if __name__ == "__main__":

@@ -286,6 +286,53 @@ def test_free_slip_reflection_with_a_storage_shift(lbm):
     assert max(errs) < 5e-6, errs
 
 
+def _freeslip_interface_case(B=8, levels=2, lid=0.02):
+    """Free-slip y and z- faces, a velocity lid on z+, periodic x; refinement in the corner x in
+    [0, n], y, z in [0, n/2] (level 2: [0, n/4]), so that level interfaces meet the free-slip faces
+    y- and z-; a sphere cut by the y- face straddles the level-1 interface at z = n/2."""
+    n = 32 if B == 8 else 64
+    k = n / 32
+    c = inputs.freeslip_box_case(n=n, B=B, lid=lid, spheres=[(8.0 * k, 1.0 * k, 16.0 * k, 4.0 * k)])
+    c["regions"] = [("box", 1, (0, 0, 0), (n, n / 2, n / 2)), ("box", 2, (0, 0, 0), (n, n / 4, n / 4))][:levels]
+    c["lmax"] = levels
+    return c, n
+
+
+@pytest.mark.parametrize("B,levels", [(8, 1), (8, 2), (16, 1)])
+def test_free_slip_faces_met_by_level_interfaces_match_the_oracle(lbm, oracle_mod, B, levels):
+    """Level interfaces meeting free-slip faces (Sec. 4.1: the boundary treatment reaches into the
+    innermost ghost layers): ghost cells next to the faces take the reflection, from mirrored
+    neighbours that are owned cells or ghost cells (exploded in sub-step 1 and in layer 3,
+    streamed otherwise).  FP64, Taylor-Green start, 30 coarse steps, against the oracle."""
+    case, n = _freeslip_interface_case(B, levels)
+    f, o = _pair(lbm, oracle_mod, case, field=inputs.taylor_green_field(n))
+    assert f.nlev == levels + 1
+    f.step_coarse(30)
+    o.step(30)
+    assert _compare(f, o) < TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32s", 3e-6), ("fp16s", 1e-3)])
+def test_uniform_flow_along_free_slip_faces_met_by_interfaces_stays_uniform(lbm, precision, tol):
+    """The paired walk's coupled cells and the ghost stream take the reflection in FP32 with the
+    storage-shift correction; a uniform flow along the faces is an exact steady state on every
+    level (free-slip faces only, so no lid).  FP64 keeps it to round-off; the shifted layouts keep
+    it to their storage rounding, accumulated over the 200 finest-level steps of 50 coarse steps
+    (the shift (0.02, 0.01, -0.01) does not match the flow, so the stored deviations are of order
+    0.01 and their FP32 rounding of order 1e-9 per step)."""
+    u = 0.03
+    case, n = _freeslip_interface_case(8, 2, lid=None)
+    case = dict(case, spheres=[], u_shift=(0.02, 0.01, -0.01))
+    g = lbm.Forest(case, precision=precision)
+    g.init_uniform((u, 0.0, 0.0))
+    g.step_coarse(50)
+    for L in range(g.nlev):
+        rho, v = g.get_macroscopic(L)
+        ok = np.isfinite(rho)
+        assert np.abs(v[0, ok] - u).max() < tol * u and np.abs(v[1:, ok]).max() < tol * u
+    g.close()
+
+
 def test_obstacle_across_an_interface_and_forced_flow(lbm, oracle_mod):
     """A sphere that straddles a level interface (ghost cells take the coarse flag), no-slip
     walls, body force, refinement touching a wall."""

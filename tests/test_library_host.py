@@ -136,12 +136,17 @@ def test_lid_scaling_forest_reproduces_the_benchmark_level_table(lbm, roots, B):
     assert sum(p.counts(L)["fluid"] for L in range(4)) == int(n.sum()) * B ** 3
 
 
-def test_a_level_interface_on_a_free_slip_face_is_rejected(lbm):
-    """Free-slip reflection reads the tangential neighbour on the same level, so every leaf that
-    touches a free-slip face must have one level; the planner rejects forests where an interface
-    meets the face (here the refined box reaches the y- face)."""
-    case = dict(inputs.freeslip_box_case(), regions=[("box", 1, (0, 0, 0), (8, 8, 8))])
-    with pytest.raises(lbm.LBMError) as ei:
-        lbm.Plan(case)
-    assert ei.value.status == lbm.LBM_EINVAL and "free-slip face" in str(ei.value)
-    lbm.Plan(inputs.freeslip_box_case())            # the centre-refined box is accepted
+@pytest.mark.parametrize("B,levels", [(8, 1), (8, 2), (16, 1)])
+def test_level_interfaces_meeting_free_slip_faces_are_planned(lbm, B, levels):
+    """Sec. 4.1 lets level transitions meet free-slip boundaries by extending the boundary
+    treatment to the ghost layers.  The planner resolves every needed free-slip mirror of an owned
+    or ghost cell within ghost layer 3 (it fails with LBM_EINVAL otherwise), so a refined corner
+    that reaches the y- and z- faces (and, with two levels, a second corner inside it) plans, with
+    ghost work on every refined level.  The GPU parity tests check the values."""
+    regions = [("box", 1, (0, 0, 0), (32, 16, 16)), ("box", 2, (0, 0, 0), (32, 8, 8))][:levels]
+    case = dict(inputs.freeslip_box_case(n=32 if B == 8 else 64, B=B), regions=regions, lmax=levels)
+    p = lbm.Plan(case)
+    assert p.nlev == levels + 1
+    for L in range(1, p.nlev):
+        w = p.ghost_work(L)
+        assert w["values1"] > 0 and w["values2"] > 0, (L, w)

@@ -111,3 +111,16 @@ def test_targets_then_fields_return_the_refined_solution(lbm):
         assert torch.allclose(u2[:, ok], u[:, ok], rtol=0, atol=1e-8)
         assert int(w.sum().item()) == int(ok.sum().item())
     fine.close()
+
+
+def test_the_trained_net_predicts_a_held_out_refined_solution_better_than_the_coarse_one(lbm):
+    """What the learned part of the warm start gains where it acts: trained on four 32^3 channels
+    (targets: each refined solution, converged from the coarse-only start), the net's prediction
+    of a fifth, held-out channel's refined levels is closer to its converged refined solution than
+    the sampled coarse solution alone (the skip term the net corrects).  The loss is the training
+    objective (weighted mean squared error of scaled rho and u on the fluid voxels)."""
+    from paper_1508_07982_gb300 import warmstart as ws
+    g = ws.heldout_gain(n_train=4, H=32, B=8, max_steps=40000, epochs=10)
+    print("warm-start net, training-set loss %s, held-out loss %s" % (g["train_set"], g["heldout"]))
+    assert g["train_set"]["net"] < g["train_set"]["coarse_only"]
+    assert g["heldout"]["net"] < g["heldout"]["coarse_only"]
