@@ -357,10 +357,15 @@ struct StepSmem {
     static constexpr bool kSep = false;
     static constexpr int SCRATCH_BYTES = 19 * 256 * int(sizeof(C));
     static constexpr int TOT_BYTES = 4 * 256 * int(sizeof(C));
+    // the FP16-storage walk also stages the link masks of each warp's rows: [WR][B] uint32 per warp
+    static constexpr int LSTAGE = (CX == 2 && sizeof(T) == 2) ? WR * B : 0;
+    static constexpr int LSTAGE_BYTES = 8 * LSTAGE * 4;
     static constexpr int kBudget = (227 * 1024) / MINB - 1024 - TOT_BYTES - 128;
-    static constexpr int kFit = kBudget / STAGE_BYTES;
+    static constexpr int kFit = kBudget / (STAGE_BYTES + LSTAGE_BYTES);
     static constexpr int S = kFit > 6 ? 6 : (kFit < 2 ? 2 : kFit);   // pipeline depth in walk steps
-    static constexpr int AREA = S * STAGE_BYTES > SCRATCH_BYTES ? S * STAGE_BYTES : SCRATCH_BYTES;
+    static constexpr int OFF_LINK = S * STAGE_BYTES;
+    static constexpr int STAGES = OFF_LINK + S * LSTAGE_BYTES;
+    static constexpr int AREA = STAGES > SCRATCH_BYTES ? STAGES : SCRATCH_BYTES;
     static constexpr int OFF_SCRATCH = 0;
     static constexpr int OFF_TOT = AREA;
     static constexpr int OFF_WALL = AREA + 4 * 256 * int(sizeof(C));   // [8][19] FP32 bounce-back terms
@@ -369,7 +374,8 @@ struct StepSmem {
     // alignment slack): the launch bound asks for no more
     static constexpr int kFitCtas = (228 * 1024) / (BYTES + 128 + 1024);
     static constexpr int kMinCtas = MINB < kFitCtas ? MINB : (kFitCtas < 1 ? 1 : kFitCtas);
-    static_assert(WSTAGE_BYTES % 16 == 0 && (RS * int(sizeof(T))) % 16 == 0, "16-byte copies need 16-byte alignment");
+    static_assert(WSTAGE_BYTES % 16 == 0 && (RS * int(sizeof(T))) % 16 == 0 && OFF_LINK % 16 == 0,
+                  "16-byte copies need 16-byte alignment");
 };
 
 // Directions with e_qx != 0, whose staged rows need the x-neighbour chunk.
@@ -773,6 +779,8 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
     const int ZC = 1 << zl;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T* wst = reinterpret_cast<T*>(smem) + warp * SP::WSTAGE;   // + s * 8 * WSTAGE
+    constexpr bool kLinkStaged = SP::LSTAGE > 0;                 // FP16 storage
+    static_assert(!kLinkStaged || WR * B / 4 == 16, "a warp's link-mask rows are 16 chunks of 16 bytes");
     C(&tot)[4][256] = *reinterpret_cast<C(*)[4][256]>(smem + SP::OFF_TOT);
     const T* src = static_cast<const T*>(a.lv.f[a.cur]);
     T* dst = static_cast<T*>(a.lv.f[a.cur ^ 1]);
@@ -805,12 +813,22 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
     const int xl = 2 * (lane % (B / 2)), row = lane / (B / 2);   // this lane's cells x, x + 1 and row
     const int c = lane % CR, rs0 = lane / CR;                     // this lane's copy chunk and first row set
     // Column data of a task group (brick, row group): which cells of this lane's two columns the
-    // walk skips (obstacle and coupled cells) and whether their link masks are needed.
+    // walk skips (obstacle and coupled cells) and whether their link masks are needed.  Two
+    // independent loads (columns x and x + 1 are adjacent); the issuing side takes them at a chunk's
+    // first task and, with FP16 storage, the consuming side reuses them.
     struct Cols {
         uint32_t sol0, sol1;
         bool nm0, nm1;
     };
     auto columns = [&](int brick, int rg) -> Cols {
+        const int col = (brick << B2s) + ((rg * WR + row) << LB) + xl;
+        const uint2 sol = __ldg(reinterpret_cast<const uint2*>(a.lv.colsolid + col));
+        const unsigned short sp = __ldg(reinterpret_cast<const unsigned short*>(a.lv.colspec + col));
+        return Cols{sol.x, sol.y, (sp & 0xFFu) != 0u, (sp >> 8) != 0u};
+    };
+    // the same, skipping plain bricks (one load fewer there, a dependent chain elsewhere): fewer
+    // registers, which the FP32-storage walk (at its register limit) needs
+    auto columns_plain = [&](int brick, int rg) -> Cols {
         Cols k{0u, 0u, false, false};
         if (!(__ldg(a.lv.kind + brick) & BK_PLAIN)) {
             const int col = (brick << B2s) + ((rg * WR + row) << LB) + xl;
@@ -866,6 +884,7 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
     // the issuing side: its chunk and next task (pointers mp / hp, column data icol)
     int ich = fetch(), ik = 0;
     Cols icol{0u, 0u, false, false};
+    bool imask = false;   // FP16 storage: some lane of the chunk needs its link masks
     // issues the next task of the issuing side into stage k % S (after the warp's last reads of that
     // stage) and commits its copies as one group (an empty group once the launch has no work left)
     auto issue = [&](int k) {
@@ -876,7 +895,12 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
         int brick, rg, z;
         task(ich, ik, brick, rg, z);
         if (ik == 0) {
-            icol = columns(brick, rg);
+            if constexpr (sizeof(T) == 2) {
+                icol = columns(brick, rg);
+                imask = __any_sync(0xffffffffu, icol.nm0 || icol.nm1);
+            } else {
+                icol = columns_plain(brick, rg);
+            }
 #pragma unroll
             for (int m = 0; m < MJ; m++) {
                 const int rs = rs0 + RPM * m;
@@ -926,6 +950,18 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
             }
             hp[mh] += 1 << B2s;
         }
+        if constexpr (kLinkStaged) {
+            // the link masks of the task's rows, where any lane of the chunk needs them: 16 lanes copy
+            // one 16-byte chunk each
+            if (imask && lane < 16) {
+                constexpr int CPR = B / 4;   // 16-byte chunks per row of masks
+                const int i = lane / CPR, cc = lane - CPR * i;
+                uint32_t* ls = reinterpret_cast<uint32_t*>(smem + SP::OFF_LINK) + ((k % S) * 8 + warp) * SP::LSTAGE;
+                if (all || ((lm >> i) & 1u))
+                    cp_async16(ls + i * B + cc * 4,
+                               a.lv.link + (int64_t(brick) << B3s) + (z << B2s) + ((rg * WR + i) << LB) + cc * 4);
+            }
+        }
         cp_async_commit();
         if (++ik == ZC) {
             ich = fetch();
@@ -959,13 +995,27 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
         __syncwarp();             // and every lane's
         int brick, rg, z;
         task(cch, ck, brick, rg, z);
-        if (ck == 0) ccol = columns(brick, rg);
+        if (ck == 0) {
+            // FP16 storage: the issuing side's copy (it is still within this chunk, S - 1 < ZC);
+            // FP32 storage loads it again, which keeps it within its registers
+            if constexpr (sizeof(T) == 2) ccol = icol;
+            else ccol = columns_plain(brick, rg);
+        }
         const bool l0 = !((ccol.sol0 >> z) & 1u), l1 = !((ccol.sol1 >> z) & 1u);
         if (l0 || l1) {
             const int y = rg * WR + row;
             const int cidx = (brick << B3s) + (z << B2s) + (y << LB) + xl;
-            const uint32_t m0 = (ccol.nm0 && l0) ? __ldg(a.lv.link + cidx) : 0u;
-            const uint32_t m1 = (ccol.nm1 && l1) ? __ldg(a.lv.link + cidx + 1) : 0u;
+            uint32_t m0, m1;
+            if constexpr (kLinkStaged) {
+                // staged with the rows (copied whenever a lane of the chunk has a masked column)
+                const uint32_t* lrow = reinterpret_cast<const uint32_t*>(smem + SP::OFF_LINK) +
+                                       ((k % S) * 8 + warp) * SP::LSTAGE + row * B + xl;
+                m0 = (ccol.nm0 && l0) ? lrow[0] : 0u;
+                m1 = (ccol.nm1 && l1) ? lrow[1] : 0u;
+            } else {
+                m0 = (ccol.nm0 && l0) ? __ldg(a.lv.link + cidx) : 0u;
+                m1 = (ccol.nm1 && l1) ? __ldg(a.lv.link + cidx + 1) : 0u;
+            }
             T* st = wst + (k % S) * 8 * SP::WSTAGE + row * 19 * RS + H + xl;   // + q * RS - e_qx
             f2 v[19];
 #pragma unroll
