@@ -276,6 +276,23 @@ lbm_status lbm_launches_per_coarse_step(const lbm_forest* f, int32_t* n);
 lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cells_per_thread_log2, int32_t* ctas_per_sm,
                         double* ms_per_step);
 
+/* Picks the block size for a description: for every B in {8, 16, 32} that divides the domain
+ * (root_blocks x block_cells level-0 cells per axis, kept fixed: root_blocks becomes N / B) it
+ * creates the forest with block size B (through `alloc`, on `stream`), sets the level parameters as
+ * lbm_set_level_params(lambda_e0, magic_lambda, accel0) does, starts it from rest, tunes its thread
+ * mapping as lbm_autotune(n_steps) does, and destroys it; it writes the B with the fewest ms per
+ * coarse step to *block_cells and each candidate's ms to ms_per_step[0..2] (B = 8, 16, 32; -1 where
+ * B does not divide the domain or the forest cannot be built).  The regions and obstacles are the
+ * same for every B, but refinement splits whole blocks, so a larger B covers the requested regions
+ * with more cells: the time per coarse step of the same problem, not GLUPS, decides.  Refinement
+ * by callback is not supported (the callback takes block coordinates, which depend on B): refine
+ * must be NULL.  LBM_EINVAL for invalid arguments or when no candidate can be built.  The paper
+ * fixes its block size per run (Sec. 3.2); this is a tuning aid. */
+lbm_status lbm_autotune_block_size(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag, void* user,
+                                   double lambda_e0, double magic_lambda, const double accel0[3], void* stream,
+                                   const lbm_allocator* alloc, int32_t n_steps, int32_t* block_cells,
+                                   double ms_per_step[3]);
+
 /* ---- batches of forests --------------------------------------------------------------------
  * Many independent forests (for example a parameter study of small cases) stepped together:
  * one coarse step of every member is Alg. 1 over the deepest member, and each phase of it (the

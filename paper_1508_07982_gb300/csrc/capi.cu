@@ -1141,6 +1141,46 @@ extern "C" lbm_status lbm_autotune(lbm_forest* f, int32_t n_steps, int32_t* cell
         [&](int n) { return lbm_step_coarse(f, n); }, cells_per_thread_log2, ctas_per_sm, ms_per_step);
 }
 
+extern "C" lbm_status lbm_autotune_block_size(const lbm_forest_desc* d, lbm_refine_fn refine, lbm_flag_fn flag,
+                                              void* user, double lambda_e0, double magic_lambda, const double accel0[3],
+                                              void* stream, const lbm_allocator* alloc, int32_t n_steps,
+                                              int32_t* block_cells, double ms_per_step[3]) {
+    if (!d || !block_cells || n_steps < 1) return fail(LBM_EINVAL, "invalid argument");
+    if (refine) return fail(LBM_EINVAL, "a refine callback takes block coordinates, which depend on the block size");
+    double ms[3] = {-1.0, -1.0, -1.0};
+    int best = -1;
+    std::string last;
+    for (int k = 0; k < 3; k++) {
+        const int B = 8 << k;
+        lbm_forest_desc e = *d;
+        bool fits = true;
+        for (int a = 0; a < 3; a++) {
+            const int64_t N = int64_t(d->root_blocks[a]) * d->block_cells;
+            fits = fits && N % B == 0;
+            e.root_blocks[a] = int32_t(N / B);
+        }
+        if (!fits) continue;
+        e.block_cells = B;
+        lbm_forest* f = nullptr;
+        lbm_status st = lbm_create_forest(&e, nullptr, flag, user, stream, alloc, &f);
+        if (!st) st = lbm_set_level_params(f, lambda_e0, magic_lambda, accel0);
+        if (!st) st = lbm_init_equilibrium(f, -1, nullptr, nullptr, 0);
+        double t = 0.0;
+        if (!st) st = lbm_autotune(f, n_steps, nullptr, nullptr, &t);
+        if (st) last = g_err;
+        lbm_destroy(f);
+        if (st == LBM_ECUDA || st == LBM_ETIMEOUT) return fail(st, "block size %d: %s", B, last.c_str());
+        if (st) continue;
+        ms[k] = t;
+        if (best < 0 || t < ms[best]) best = k;
+    }
+    if (ms_per_step)
+        for (int k = 0; k < 3; k++) ms_per_step[k] = ms[k];
+    if (best < 0) return fail(LBM_EINVAL, "no block size could be built%s%s", last.empty() ? "" : ": ", last.c_str());
+    *block_cells = 8 << best;
+    return LBM_OK;
+}
+
 // ------------------------------------------------------------------ batches of forests
 namespace {
 

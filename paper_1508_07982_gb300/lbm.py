@@ -28,7 +28,8 @@ EXPORTS = [
     "lbm_set_level_params_explicit", "lbm_init_equilibrium", "lbm_step_coarse", "lbm_get_macroscopic",
     "lbm_get_pdfs", "lbm_set_pdfs", "lbm_reduce_mass_momentum", "lbm_timing_begin", "lbm_timing_end",
     "lbm_launches_per_coarse_step", "lbm_set_kernel_config", "lbm_get_kernel_config",
-    "lbm_mass_momentum_noalloc", "lbm_probe_fp64_fma", "lbm_autotune", "lbm_batch_create", "lbm_batch_step",
+    "lbm_mass_momentum_noalloc", "lbm_probe_fp64_fma", "lbm_autotune", "lbm_autotune_block_size",
+    "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_set_kernel_config", "lbm_batch_autotune", "lbm_batch_cell_updates_per_coarse_step",
     "lbm_batch_launches_per_coarse_step", "lbm_batch_destroy", "lbm_net_create", "lbm_net_destroy",
     "lbm_net_num_params", "lbm_net_get_params", "lbm_net_set_params", "lbm_net_forward", "lbm_net_predict",
@@ -150,6 +151,8 @@ def library():
             "lbm_get_kernel_config": [P, i32p, i32p],
             "lbm_mass_momentum_noalloc": [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, dp, P, P],
             "lbm_autotune": [P, ctypes.c_int32, i32p, i32p, dp],
+            "lbm_autotune_block_size": [ctypes.POINTER(Desc), REFINE_FN, FLAG_FN, P, ctypes.c_double, ctypes.c_double,
+                                        dp, P, ctypes.POINTER(Allocator), ctypes.c_int32, i32p, dp],
             "lbm_batch_create": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(Allocator), ctypes.POINTER(P)],
             "lbm_batch_step": [P, ctypes.c_int32],
             "lbm_batch_set_kernel_config": [P, ctypes.c_int32, ctypes.c_int32],
@@ -281,6 +284,23 @@ def lbm_mass_momentum_noalloc(pdfs, precision, n_cells, rho0, out, stream=None, 
     _check(library().lbm_mass_momentum_noalloc(ctypes.c_void_p(p), PRECISION[precision], n_cells, rho0,
                                                 _dp(us) if us is not None else None, ctypes.c_void_p(o),
                                                 ctypes.c_void_p(stream)))
+
+
+def autotune_block_size(case, precision="fp32s", n_steps=10, flag=None, stream=None, allocator="torch"):
+    """lbm_autotune_block_size: the block size (8, 16 or 32) with the fewest ms per coarse step for
+    this case's domain, regions and obstacles, and the ms of each candidate (-1: not buildable)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    d = make_desc(case, precision)
+    fl = FLAG_FN(flag) if flag else FLAG_FN()
+    acc = np.ascontiguousarray(case.get("accel", (0.0, 0.0, 0.0)), dtype=np.float64)
+    b = ctypes.c_int32()
+    ms = np.zeros(3)
+    _check(library().lbm_autotune_block_size(ctypes.byref(d), REFINE_FN(), fl, None, float(case["lambda_e0"]),
+                                             float(case.get("magic", 3.0 / 16.0)), _dp(acc), ctypes.c_void_p(stream),
+                                             _allocator(allocator), n_steps, ctypes.byref(b), _dp(ms)))
+    return b.value, {8: ms[0], 16: ms[1], 32: ms[2]}
 
 
 class Plan:

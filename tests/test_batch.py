@@ -6,6 +6,8 @@ batched and single stepping bit for bit (same kernels, same arithmetic), and one
 against the oracle.  The CPU tests check the batched workload's seeded case generator against
 the library's forest planner.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -42,6 +44,18 @@ def test_batch_cases_are_seeded_balanced_and_in_range(lbm_host):
         p = lbm_host.Plan(c)
         assert p.nlev == c["lmax"] + 1
         assert sum(p.counts(L)["blocks"] for L in range(p.nlev)) == c["leaves"]
+
+
+def test_block_size_tuner_rejects_a_refine_callback_before_any_cuda_call(lbm_host):
+    """A refine callback takes block coordinates, which change with the block size, so the tuner
+    refuses it (LBM_EINVAL) before it creates a forest."""
+    case = inputs.periodic_case(n=64, B=16, regions=[("box", 1, (16, 16, 16), (48, 48, 48))], lmax=1)
+    d = lbm_host.make_desc(case, "fp32s")
+    cb = lbm_host.REFINE_FN(lambda L, x, y, z, u: 0)
+    b = ctypes.c_int32()
+    st = lbm_host.library().lbm_autotune_block_size(ctypes.byref(d), cb, lbm_host.FLAG_FN(), None, 1.6,
+                                                    3 / 16, None, None, None, 2, ctypes.byref(b), None)
+    assert st == lbm_host.LBM_EINVAL and "refine callback" in lbm_host.library().lbm_last_error().decode()
 
 
 def test_batch_cases_match_the_oracle_forest(lbm_host, oracle_mod):
@@ -129,6 +143,37 @@ def test_batch_member_matches_the_oracle(lbm, oracle_mod):
 
 
 @pytest.mark.gpu
+def test_fp32s_batch_member_error_against_the_oracle(lbm, oracle_mod):
+    """The batched workload runs in FP32S storage; its error against the FP64 oracle is stated: a
+    3-level member, 20 coarse steps from rest, velocity within 1e-5 of the lid speed and density
+    within 1e-6 on every owned fluid cell (FP32 rounding of the stored deviations, of order 1e-7
+    relative, accumulated over 80 finest steps)."""
+    cases = inputs.batch_cases(n=8, seed=5)
+    deep = next(i for i, c in enumerate(cases) if c["lmax"] == 2)
+    fs = _forests(lbm, cases, "fp32s")
+    o = oracle_mod.Oracle(cases[deep])
+    o.init_fields(inputs.uniform_field())
+    b = lbm.Batch(fs)
+    b.step(20)
+    o.step(20)
+    f = fs[deep]
+    lid = cases[deep]["bc_u"][5][0]
+    du = dr = 0.0
+    for L in range(f.nlev):
+        rho, u = f.get_macroscopic(L)
+        X, Y, Z = f.cell_coords(L)
+        idx = o.lookup(L, X, Y, Z)
+        rr, ur = o.macro(L)
+        ok = np.isfinite(rho)
+        for k in range(3):
+            du = max(du, float(np.abs(u[k][ok] - ur[k][idx][ok]).max()))
+        dr = max(dr, float(np.abs(rho[ok] - rr[idx][ok]).max()))
+    print("FP32S batch member against the oracle: u L-inf / lid %.3e, rho L-inf %.3e" % (du / lid, dr))
+    assert du / lid < 1e-5 and dr < 1e-6
+    b.close()
+
+
+@pytest.mark.gpu
 def test_autotune_leaves_the_state_and_results_unchanged(lbm):
     case = inputs.sphere_channel_case(H=32, B=16, radii=(20.0, 12.0, 6.5))
     f = lbm.Forest(case, precision="fp32s")
@@ -163,6 +208,21 @@ def test_batch_autotune_keeps_members_in_step(lbm):
         for L in range(fa.nlev):
             assert _same(fa.get_pdfs(L), fb.get_pdfs(L))
     b.close()
+
+
+@pytest.mark.gpu
+def test_block_size_tuner_times_every_candidate_and_keeps_the_fastest(lbm):
+    """The block-size tuner builds the case with 8^3, 16^3 and 32^3 blocks (the same 64^3 domain and
+    refined box), tunes and times each, and returns the fastest; the case itself is unchanged."""
+    case = inputs.periodic_case(n=64, B=16, collision="trt", omega=1.7,
+                                regions=[("box", 1, (16, 16, 16), (48, 48, 48))], lmax=1)
+    B, ms = lbm.autotune_block_size(case, "fp32s", n_steps=3)
+    assert set(ms) == {8, 16, 32} and all(v > 0 for v in ms.values()), ms
+    assert B in (8, 16, 32) and ms[B] == min(ms.values())
+    # a domain that 32 does not divide leaves that candidate out
+    case48 = inputs.periodic_case(n=48, B=16, collision="trt", omega=1.7)
+    B48, ms48 = lbm.autotune_block_size(case48, "fp32s", n_steps=2)
+    assert ms48[32] == -1 and ms48[8] > 0 and ms48[16] > 0 and B48 in (8, 16)
 
 
 @pytest.mark.gpu
