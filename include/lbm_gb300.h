@@ -175,7 +175,9 @@ lbm_status lbm_destroy(lbm_forest* f);
 lbm_status lbm_num_levels(const lbm_forest* f, int32_t* n_levels);
 
 /* Leaf blocks of `level` as (bx, by, bz) triples: the block-major order of every per-level
- * array.  Pass blocks = NULL to query the count into *n. */
+ * array: the traversal of the forest of octrees, root blocks in x-fastest order and, within each
+ * root, the Morton (z-order) curve (Sec. 3.3, 4.5); level 0 is the root grid, x fastest.  Pass
+ * blocks = NULL to query the count into *n. */
 lbm_status lbm_get_block_table(const lbm_forest* f, int32_t level, int32_t* n, int32_t* blocks);
 
 /* Cell updates of one coarse step: sum over levels of owned fluid cells x 2^L (every level

@@ -151,41 +151,69 @@ struct Builder {
         return flag && flag(L, c[0], c[1], c[2], user) != 0;
     }
 
+    // Position of level-L block (x, y, z) in the traversal of the forest of octrees: its root block
+    // in x-fastest order, then the Morton (z-order) key of its place within that root's octree, the
+    // bits of the three coordinates interleaved, x lowest.  The paper linearises its blocks this way,
+    // along a space-filling curve (Morton or Hilbert order), for load balancing (Sec. 3.3, 4.5);
+    // here it is the order of every per-level block list (level 0: the roots, x fastest).
+    uint64_t forest_key(int L, int x, int y, int z) const {
+        const int* n0 = p.lv[0].nb;
+        const uint64_t root = (uint64_t(z >> L) * n0[1] + uint64_t(y >> L)) * n0[0] + uint64_t(x >> L);
+        uint64_t k = 0;
+        for (int b = 0; b < L; b++)
+            k |= (uint64_t((x >> b) & 1) << (3 * b)) | (uint64_t((y >> b) & 1) << (3 * b + 1)) |
+                 (uint64_t((z >> b) & 1) << (3 * b + 2));
+        return (root << (3 * L)) | k;
+    }
+
     bool bricks(int L, std::string& err) {
         HostLevel& V = p.lv[L];
         const int B = p.B, B3 = B * B * B;
         const int64_t ngrid = int64_t(V.nb[0]) * V.nb[1] * V.nb[2];
         std::vector<int32_t> index(size_t(ngrid), -1);
-        // owned bricks: the leaves of this level, x fastest
+        // the positions of a scan in the order of the forest's traversal
+        std::vector<std::pair<uint64_t, int64_t>> order;
+        order.reserve(size_t(ngrid));
         for (int z = 0; z < V.nb[2]; z++)
             for (int y = 0; y < V.nb[1]; y++)
-                for (int x = 0; x < V.nb[0]; x++)
-                    if (state(L, x, y, z) == LEAF) {
-                        index[lin(L, x, y, z)] = int32_t(V.pos.size() / 3);
-                        V.pos.insert(V.pos.end(), {x, y, z});
-                    }
+                for (int x = 0; x < V.nb[0]; x++) order.push_back({forest_key(L, x, y, z), lin(L, x, y, z)});
+        std::sort(order.begin(), order.end());
+        auto xyz = [&](int64_t i, int& x, int& y, int& z) {
+            x = int(i % V.nb[0]);
+            y = int((i / V.nb[0]) % V.nb[1]);
+            z = int(i / (int64_t(V.nb[0]) * V.nb[1]));
+        };
+        // owned bricks: the leaves of this level, in traversal order
+        for (const auto& o : order) {
+            int x, y, z;
+            xyz(o.second, x, y, z);
+            if (state(L, x, y, z) == LEAF) {
+                index[o.second] = int32_t(V.pos.size() / 3);
+                V.pos.insert(V.pos.end(), {x, y, z});
+            }
+        }
         V.nown = int(V.pos.size() / 3);
-        // ghost bricks: coarser-covered positions touching an owned brick
+        // ghost bricks: coarser-covered positions touching an owned brick, in traversal order
         if (L > 0) {
-            for (int z = 0; z < V.nb[2]; z++)
-                for (int y = 0; y < V.nb[1]; y++)
-                    for (int x = 0; x < V.nb[0]; x++) {
-                        if (state(L, x, y, z) != ABSENT) continue;
-                        bool touch = false;
-                        for (int o = 0; o < 27 && !touch; o++) {
-                            int b[3] = {x + o % 3 - 1, y + (o / 3) % 3 - 1, z + o / 9 - 1};
-                            if (o == 13 || !wrap(L, b)) continue;
-                            int32_t k = index[lin(L, b[0], b[1], b[2])];
-                            touch = k >= 0 && k < V.nown;
-                        }
-                        if (!touch) continue;
-                        if (state(L - 1, x >> 1, y >> 1, z >> 1) != LEAF) {
-                            err = "a block next to a leaf is covered by a leaf two levels coarser";
-                            return false;
-                        }
-                        index[lin(L, x, y, z)] = int32_t(V.pos.size() / 3);
-                        V.pos.insert(V.pos.end(), {x, y, z});
-                    }
+            for (const auto& oo : order) {
+                int x, y, z;
+                xyz(oo.second, x, y, z);
+                if (state(L, x, y, z) != ABSENT) continue;
+                bool touch = false;
+                for (int o = 0; o < 27 && !touch; o++) {
+                    int b[3] = {x + o % 3 - 1, y + (o / 3) % 3 - 1, z + o / 9 - 1};
+                    if (o == 13 || !wrap(L, b)) continue;
+                    int32_t k = index[lin(L, b[0], b[1], b[2])];
+                    touch = k >= 0 && k < V.nown;
+                }
+                if (!touch) continue;
+                if (state(L - 1, x >> 1, y >> 1, z >> 1) != LEAF) {
+                    err = "a block next to a leaf is covered by a leaf two levels coarser";
+                    return false;
+                }
+                index[lin(L, x, y, z)] = int32_t(V.pos.size() / 3);
+                V.pos.insert(V.pos.end(), {x, y, z});
+            }
         }
         const int nbk = int(V.pos.size() / 3);
         V.nghost = nbk - V.nown;
