@@ -226,6 +226,7 @@ def _roofline(f, lev, precision, peaks, peak_kind):
 # its fluid cells.  The peak is measured on the device by lbm_probe_fp64_fma (independent FMA chains
 # on every SM), once per run.
 FP64_INST_PER_UPDATE = 161
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline)
 _FP64_PEAK = {}
 
 
@@ -633,6 +634,12 @@ def main():
     value = _job_value(world, upd, args.steps, ms)
     roof = _roofline(f, lev, args.precision, peaks, peak_kind)
     roof["kernel_timing_pass_ms_per_step"] = round(ms_k / args.steps, 5)
+    # the whole coarse step (graph replay: every level, explosions, side work) at the algorithmic
+    # bytes of its cell updates, against the measured and the nominal bandwidth
+    step_gbs = upd * 2 * 19 * BYTES_PER_VALUE[args.precision] / (ms / args.steps / 1e3) / 1e9
+    roof["whole_step"] = {"achieved": round(step_gbs, 1), "unit": "GB/s", "frac": round(step_gbs / roof["peak"], 4),
+                          "frac_of_nominal_7900": round(step_gbs / NOMINAL_HBM_GBS, 4)}
+    roof["frac_of_nominal_7900"] = round(roof["achieved"] / NOMINAL_HBM_GBS, 4)
     cfg = _config(case, f)
     mass = f.reduce_mass_momentum()
 
