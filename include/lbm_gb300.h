@@ -422,9 +422,8 @@ lbm_status lbm_net_set_wait_test(lbm_net* n, int32_t on);
 
 /* ---- totals without allocation ------------------------------------------------------------
  * The paper has no counterpart: this entry point serves callers that cannot allocate device
- * memory when they need mass and momentum totals (code running during CUDA stream capture,
- * where cudaMalloc is not allowed; runtimes that own all device memory through their own pool;
- * hosts that forbid dynamic allocation after start-up).  It calls no cudaMalloc, cudaFree or
+ * memory when they need mass and momentum totals (runtimes that own all device memory through
+ * their own pool; hosts that forbid dynamic allocation after start-up).  It calls no cudaMalloc, cudaFree or
  * other allocating routine.  Its per-CTA partial sums live in one fixed device array of
  * (LBM_NOALLOC_MAX_CELLS / LBM_NOALLOC_CELLS_PER_CTA) x 5 doubles = 640 KiB, which every GPU that
  * loads the library holds until the process exits.
@@ -446,7 +445,7 @@ lbm_status lbm_net_set_wait_test(lbm_net* n, int32_t on);
  * as given, so callers with a body force subtract rho0 a per fluid cell themselves.
  * A CUDA error already pending when the call starts is returned as LBM_ECUDA without launching.
  * The first call on each device looks up the device address of the fixed array
- * (cudaGetSymbolAddress); make that first call before capturing any stream on that device.
+ * (cudaGetSymbolAddress, which allocates nothing).
  * All calls share the array and it keeps the last call's partial sums; every call writes each
  * slot it reads, so nothing has to be cleared, but calls that overlap on the GPU (other streams
  * or threads without ordering between them) race on it and return wrong totals. */

@@ -1,10 +1,9 @@
 // Mass and momentum totals of a caller-owned PDF array, with no allocation of any kind.
 //
-// Some callers cannot allocate device memory at the time they need the totals: code running
-// while a CUDA stream is being captured into a graph (cudaMalloc is not permitted there),
-// runtimes that hand out all device memory from their own pre-sized pool and forbid the
-// CUDA allocator after start-up, and embedded or safety-certified hosts that allow no
-// dynamic allocation once initialised.  The regular lbm_reduce_mass_momentum keeps its
+// Some callers cannot allocate device memory at the time they need the totals: runtimes that
+// hand out all device memory from their own pre-sized pool and forbid the CUDA allocator after
+// start-up, and embedded or safety-certified hosts that allow no dynamic allocation once
+// initialised.  The regular lbm_reduce_mass_momentum keeps its
 // per-CTA partial sums in memory that lbm_create_forest allocated; this entry point instead
 // keeps them in one file-scope device array of fixed size, reserved when the library is
 // loaded, so the call itself allocates nothing.

@@ -1,8 +1,8 @@
 """The allocation-free totals entry point, lbm_mass_momentum_noalloc.
 
 It exists for callers that cannot allocate device memory when they need the mass and momentum
-totals (during CUDA stream capture, under a runtime that owns all device memory, or on a host
-that forbids allocation after start-up).  Its scratch is a fixed device array inside the library.
+totals (under a runtime that owns all device memory, or on a host that forbids allocation after
+start-up).  Its scratch is a fixed device array inside the library.
 These tests compare it, through the C-ABI, with the regular lbm_reduce_mass_momentum on the same
 state, on two calls in a row so that a second call sees the array the first one left behind, and
 with FP64 sums on the host where obstacle cells (NaN) must be skipped and counted.
