@@ -899,7 +899,7 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
                 icol = columns(brick, rg);
                 imask = __any_sync(0xffffffffu, icol.nm0 || icol.nm1);
             } else {
-                icol = columns_plain(brick, rg);
+                icol = columns(brick, rg);
             }
 #pragma unroll
             for (int m = 0; m < MJ; m++) {
@@ -999,7 +999,7 @@ __device__ __forceinline__ void walk_packed(const StepArgs& a, int cta, int ncta
             // FP16 storage: the issuing side's copy (it is still within this chunk, S - 1 < ZC);
             // FP32 storage loads it again, which keeps it within its registers
             if constexpr (sizeof(T) == 2) ccol = icol;
-            else ccol = columns_plain(brick, rg);
+            else ccol = columns(brick, rg);
         }
         const bool l0 = !((ccol.sol0 >> z) & 1u), l1 = !((ccol.sol1 >> z) & 1u);
         if (l0 || l1) {
